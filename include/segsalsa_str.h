@@ -1,0 +1,167 @@
+/*
+ * segsalsa_str.h -- C ABI of the GB300 (sm_103a) SegSALSA-STR solver.
+ *
+ * SegSALSA-STR (Condessa, Bioucas-Dias, Kovacevic, arXiv 1504.07028) computes the marginal MAP
+ * hidden field z of problem (7),
+ *
+ *     min_z  sum_i -ln(p_i^T z_i) + lambda sum_i ||[J z]_i||_{S_p}   s.t. z >= 0, 1_K^T z = 1,
+ *
+ * by the SALSA/ADMM iteration (12)-(14) on the split G = [I; J; I; I] of eqs. (9)-(11):
+ * a linear z-update with G^T G = 3 I + J^T J (cyclic convolutions, Sec. 4), the Moreau
+ * proximity operators of g1..g4 (eq. 10, Sec. 4), and the scaled dual update (14). J is the
+ * patch-based Jacobian of eq. (4): for a (2M+1)x(2M+1) patch (L = (2M+1)^2 shifts), [Jz]_i is
+ * the (L K) x 2 matrix of weighted shifted horizontal / vertical forward differences.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an int status (segsalsa_status); 0 is success. The message of the
+ *    last failure on a handle is available from segsalsa_str_last_error().
+ *  - Arguments are checked on the host before any launch. A failed check changes no state.
+ *  - Element type: a handle created with precision SEGSALSA_FP32 takes and returns float
+ *    arrays; SEGSALSA_FP64 takes and returns double arrays (the `const void*` / `void*`
+ *    arguments below). Labels are always int32.
+ *  - on_device = 1 means the pointer is device memory of the handle's device (for instance a
+ *    torch tensor's data_ptr()); 0 means host memory (pageable or pinned). Copies to and from
+ *    host memory are synchronous with respect to the call.
+ *  - Device work runs on the handle's stream: the stream given at creation (borrowed, never
+ *    destroyed) or a stream the library creates. Calls return after their work has completed
+ *    on that stream unless stated otherwise.
+ *  - A handle is not thread-safe; separate handles are independent.
+ *  - Periodic boundary conditions and forward differences throughout (the cyclic
+ *    convolutions of Sec. 4).
+ *
+ * Layouts
+ *  - SEGSALSA_LAYOUT_KHW: class-major (K, H, W), the paper's K x n hidden field.
+ *  - SEGSALSA_LAYOUT_HWK: pixel-major (H, W, K), the library's own layout.
+ *  - Internal state arrays exposed by get_state / set_state are pixel-major:
+ *    z, d1, d3, d4, rhs: (H, W, K); d2: (H, W, L, K, 2) with shift j row-major over
+ *    (dy, dx) in [-M, M]^2 and the last axis (horizontal, vertical) difference.
+ */
+#ifndef SEGSALSA_STR_H
+#define SEGSALSA_STR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct segsalsa_str segsalsa_str_t; /* opaque; owned by the library */
+
+typedef enum {
+  SEGSALSA_OK = 0,
+  SEGSALSA_ERR_ARG = -1,     /* invalid argument; nothing was changed */
+  SEGSALSA_ERR_OOM = -2,     /* device allocation failed or workspace too small */
+  SEGSALSA_ERR_CUDA = -3,    /* a CUDA runtime call failed; the message names it */
+  SEGSALSA_ERR_NUMERIC = -4, /* non-finite values appeared in the iterates */
+  SEGSALSA_ERR_TIMEOUT = -5, /* reserved for bounded device-side waits */
+  SEGSALSA_ERR_STATE = -6    /* call out of order (e.g. solve before set_probs) */
+} segsalsa_status;
+
+enum { SEGSALSA_FP32 = 0, SEGSALSA_FP64 = 1 };
+enum { SEGSALSA_LAYOUT_KHW = 0, SEGSALSA_LAYOUT_HWK = 1 };
+enum { SEGSALSA_SCHATTEN_INF = 0 }; /* schatten_p value meaning p = infinity */
+
+/* Problem statement of eq. (7) and the SALSA penalty of eq. (13). */
+typedef struct {
+  int32_t H, W;          /* image size; H, W >= 2M+2                                      */
+  int32_t K;             /* number of classes, 2 <= K <= 32                               */
+  int32_t M;             /* patch half-width: (2M+1)x(2M+1) patch, 0 <= M <= 2.
+                            M = 0 is the 1x1 patch, i.e. SegSALSA with the VTV prior (Sec. 3) */
+  const double* weights; /* L = (2M+1)^2 shift weights omega_j (row-major over (dy, dx)),
+                            host memory, copied at creation; NULL selects the Gaussian
+                            omega_j = sqrt(g_j), g_j = exp(-|s_j|^2/(2 sigma^2)) / sum        */
+  double sigma;          /* Gaussian bandwidth used when weights == NULL, > 0               */
+  double lambda;         /* prior weight lambda of eq. (7), >= 0                            */
+  double mu;             /* ADMM penalty mu of eq. (13), > 0                                */
+  int32_t schatten_p;    /* 1, 2, or SEGSALSA_SCHATTEN_INF (Sec. 3 norm, Sec. 4 MPO of g2)  */
+  int32_t precision;     /* SEGSALSA_FP32 or SEGSALSA_FP64                                  */
+  void* stream;          /* cudaStream_t to run on (borrowed), or NULL for a library stream */
+} segsalsa_str_params;
+
+/* Device bytes a handle with these parameters needs when the caller provides the memory.
+ * Returns SEGSALSA_ERR_ARG for invalid parameters. */
+int segsalsa_str_workspace_bytes(const segsalsa_str_params* params, size_t* bytes);
+
+/* Create a solver handle. If `workspace` is non-NULL it must be device memory of at least
+ * segsalsa_str_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept alive
+ * until destroy; otherwise the library allocates (and later frees) its own. The handle uses
+ * the current CUDA device. On failure *out is set to NULL. */
+int segsalsa_str_create(const segsalsa_str_params* params, void* workspace,
+                        size_t workspace_bytes, segsalsa_str_t** out);
+
+/* Set the class probabilities p_i of eq. (7) and reset the iteration: z^0 = p_i / 1^T p_i,
+ * u^0 = G z^0, d^0 = 0 (iteration counter 0). p has H*W*K elements in `layout`. Every entry
+ * must be finite and >= 0 and every pixel needs a positive entry, so that p_i^T z_i > 0 is
+ * reachable (Sec. 4, feasible set of eq. 7); otherwise SEGSALSA_ERR_ARG and nothing changes.
+ * p need not sum to one: the iterates are invariant to a positive per-pixel scale of p. */
+int segsalsa_str_set_probs(segsalsa_str_t* h, const void* p, int32_t layout, int32_t on_device);
+
+/* Run `iters` >= 0 SALSA iterations (12)-(14), continuing from the current state.
+ * If `trace` is non-NULL (host memory), every `trace_every` iterations (and after the last
+ * one) a record of 6 doubles is written:
+ *   (k, primal residual ||G z^k - u^k||, dual residual mu ||G^T (u^k - u^{k-1})||,
+ *    objective (7) at the simplex projection of z^k, min z^k, max_i |1^T z_i^k - 1|)
+ * The caller provides room for floor(iters / trace_every) + 1 records; *n_records (nullable)
+ * receives the count. trace_every must be >= 1 when trace is non-NULL. The stopping rule of
+ * Sec. 4 (residuals below a threshold) is left to the caller: the solver runs a fixed count.
+ * Returns SEGSALSA_ERR_NUMERIC if non-finite values appear in a traced record. */
+int segsalsa_str_solve(segsalsa_str_t* h, int32_t iters, double* trace, int32_t trace_every,
+                       int32_t* n_records);
+
+/* Label readout argmax_k z_k of every pixel (link p(y_i = k | z_i) = [z_i]_k, Sec. 2; ties to
+ * the lowest k), H*W int32 in row-major pixel order. */
+int segsalsa_str_get_labels(segsalsa_str_t* h, int32_t* labels, int32_t on_device);
+
+/* Current hidden field z (H*W*K elements in `layout`). */
+int segsalsa_str_get_z(segsalsa_str_t* h, void* z, int32_t layout, int32_t on_device);
+
+/* Number of iterations run since the last set_probs / set_state. */
+int segsalsa_str_get_iteration(const segsalsa_str_t* h, int32_t* k);
+
+/* Checkpoint: copy out the solver state after k iterations: z^k, d1^k..d4^k and
+ * rhs^k = G^T (u^k + d^k) (the right-hand side of the next z-update, eq. 12), in the
+ * pixel-major layouts of the header comment. Any pointer may be NULL to skip it. rhs^k is
+ * undefined when k = 0 (the next z-update is the identity then). */
+int segsalsa_str_get_state(segsalsa_str_t* h, void* z, void* d1, void* d2, void* d3, void* d4,
+                           void* rhs, int32_t on_device);
+
+/* Resume: load a state written by get_state (or computed elsewhere) as iteration k >= 0.
+ * z, d1..d4 are required; rhs is required when k > 0 and ignored when k = 0. The class
+ * probabilities of the last set_probs stay in use. */
+int segsalsa_str_set_state(segsalsa_str_t* h, const void* z, const void* d1, const void* d2,
+                           const void* d3, const void* d4, const void* rhs, int32_t k,
+                           int32_t on_device);
+
+/* The z-update operator alone: z = (3 I + J^T J)^{-1} rhs (eq. 12 with G^T G = 3I + J^T J),
+ * rhs and z pixel-major (H, W, K). Leaves the solver state untouched. */
+int segsalsa_str_linear_solve(segsalsa_str_t* h, const void* rhs, void* z, int32_t on_device);
+
+/* Measurement hooks. set_profiling(1) records CUDA events around each kernel launch of
+ * solve() so that kernel_stats() can report, per kernel kind, the launch count and the total
+ * device time in milliseconds since the last reset. Kernel kinds (index):
+ *   0 fused sweep (prox + dual + rhs partials), 1 row FFT forward (with partial gather),
+ *   2 column solve, 3 row FFT inverse, 4 diagnostics (residual / objective), 5 other.
+ * launches and ms point to arrays of at least 6 entries (host memory). kernel_stats works
+ * with profiling off too; then ms is not filled. reset_stats zeroes both. */
+int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on);
+int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms);
+int segsalsa_str_reset_stats(segsalsa_str_t* h);
+
+/* Algorithmic device bytes moved by one fused-sweep launch and one full iteration (the
+ * minimum traffic model: every array read or written once, no halo or pass overhead). */
+int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
+                               double* iteration_bytes);
+
+/* Release the handle and everything the library allocated for it. NULL is a no-op. */
+void segsalsa_str_destroy(segsalsa_str_t* h);
+
+/* Message of the last failed call on `h` ("" if none); for h == NULL, the last failure of
+ * segsalsa_str_create / segsalsa_str_workspace_bytes in this process. */
+const char* segsalsa_str_last_error(const segsalsa_str_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEGSALSA_STR_H */

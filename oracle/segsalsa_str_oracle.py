@@ -273,23 +273,29 @@ def initial_state(p: np.ndarray, omega, M) -> SalsaState:
     return SalsaState(z0, u0, d0, 0)
 
 
-def salsa_step(st: SalsaState, p, lam, mu, omega, M, sp):
-    """One SALSA iteration (12)-(14). Returns (new state, primal residual, dual residual)."""
+def u_d_update(z, d, p, lam, mu, omega, M, sp):
+    """Eqs. (13)-(14) given z^{k+1}: the four decoupled MPOs at v = G z^{k+1} - d^k, then
+    d^{k+1} = d^k - (G z^{k+1} - u^{k+1}). Returns (u^{k+1}, d^{k+1}, G z^{k+1})."""
     L = len(omega)
     K, H, W = p.shape
-    # (12) z^{k+1} = argmin ||G z - u^k - d^k||^2  <=>  G^T G z = G^T (u^k + d^k)
-    z = linear_solve(st.rhs(omega, M), omega, M)
     Gz = apply_G(z, omega, M)
-    v = [a - b for a, b in zip(Gz, st.d)]
-    # (13) u^{k+1}: the four decoupled MPOs at G z^{k+1} - d^k
+    v = [a - b for a, b in zip(Gz, d)]
     u1 = prox_g1(v[0], p, mu)
     V2 = jacobian_matrices(v[1])
     u2 = from_jacobian_matrices(prox_g2(V2, lam / mu, sp), L, K, H, W)
     u3 = prox_g3(v[2])
     u4 = prox_g4(v[3])
     u = [u1, u2, u3, u4]
-    # (14) d^{k+1} = d^k - (G z^{k+1} - u^{k+1})
-    d = [dj - (gj - uj) for dj, gj, uj in zip(st.d, Gz, u)]
+    dn = [dj - (gj - uj) for dj, gj, uj in zip(d, Gz, u)]
+    return u, dn, Gz
+
+
+def salsa_step(st: SalsaState, p, lam, mu, omega, M, sp):
+    """One SALSA iteration (12)-(14). Returns (new state, primal residual, dual residual)."""
+    # (12) z^{k+1} = argmin ||G z - u^k - d^k||^2  <=>  G^T G z = G^T (u^k + d^k)
+    z = linear_solve(st.rhs(omega, M), omega, M)
+    # (13), (14)
+    u, d, Gz = u_d_update(z, st.d, p, lam, mu, omega, M, sp)
     primal = _norm2([gj - uj for gj, uj in zip(Gz, u)])
     dual = mu * _norm2([apply_GT([a - b for a, b in zip(u, st.u)], omega, M)])
     return SalsaState(z, u, d, st.k + 1), primal, dual

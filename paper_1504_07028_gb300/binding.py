@@ -1,0 +1,287 @@
+"""Thin Python binding of the C ABI in include/segsalsa_str.h (ctypes; argument marshalling only).
+
+Every compute step runs in libsegsalsa_str.so. Arrays may be numpy arrays (host memory) or
+torch tensors (device tensors are passed by data_ptr() with on_device=1). There is no CPU
+fallback: if the shared library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SEGSALSA_OK = 0
+SEGSALSA_ERR_ARG = -1
+SEGSALSA_ERR_OOM = -2
+SEGSALSA_ERR_CUDA = -3
+SEGSALSA_ERR_NUMERIC = -4
+SEGSALSA_ERR_TIMEOUT = -5
+SEGSALSA_ERR_STATE = -6
+SEGSALSA_FP32 = 0
+SEGSALSA_FP64 = 1
+SEGSALSA_LAYOUT_KHW = 0
+SEGSALSA_LAYOUT_HWK = 1
+SEGSALSA_SCHATTEN_INF = 0
+
+KERNEL_KINDS = ("sweep", "row_fft_forward", "column_solve", "row_fft_inverse", "diagnostics",
+                "other")
+
+SYMBOLS = (
+    "segsalsa_str_workspace_bytes", "segsalsa_str_create", "segsalsa_str_set_probs",
+    "segsalsa_str_solve", "segsalsa_str_get_labels", "segsalsa_str_get_z",
+    "segsalsa_str_get_iteration", "segsalsa_str_get_state", "segsalsa_str_set_state",
+    "segsalsa_str_linear_solve", "segsalsa_str_set_profiling", "segsalsa_str_kernel_stats",
+    "segsalsa_str_reset_stats", "segsalsa_str_traffic_model", "segsalsa_str_destroy",
+    "segsalsa_str_last_error",
+)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("H", C.c_int32), ("W", C.c_int32), ("K", C.c_int32), ("M", C.c_int32),
+        ("weights", C.POINTER(C.c_double)), ("sigma", C.c_double), ("lambda_", C.c_double),
+        ("mu", C.c_double), ("schatten_p", C.c_int32), ("precision", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+class SegsalsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"segsalsa_str error {code}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libsegsalsa_str.so (built in-tree by paper_1504_07028_gb300.build)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run paper_1504_07028_gb300.build.build() first")
+    lib = C.CDLL(p)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "segsalsa_str_workspace_bytes": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_size_t)]),
+        "segsalsa_str_create": (C.c_int, [C.POINTER(Params), vp, C.c_size_t, C.POINTER(vp)]),
+        "segsalsa_str_set_probs": (C.c_int, [vp, vp, i32, i32]),
+        "segsalsa_str_solve": (C.c_int, [vp, i32, C.POINTER(C.c_double), i32, C.POINTER(i32)]),
+        "segsalsa_str_get_labels": (C.c_int, [vp, vp, i32]),
+        "segsalsa_str_get_z": (C.c_int, [vp, vp, i32, i32]),
+        "segsalsa_str_get_iteration": (C.c_int, [vp, C.POINTER(i32)]),
+        "segsalsa_str_get_state": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, i32]),
+        "segsalsa_str_set_state": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, i32, i32]),
+        "segsalsa_str_linear_solve": (C.c_int, [vp, vp, vp, i32]),
+        "segsalsa_str_set_profiling": (C.c_int, [vp, i32]),
+        "segsalsa_str_kernel_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(C.c_double)]),
+        "segsalsa_str_reset_stats": (C.c_int, [vp]),
+        "segsalsa_str_traffic_model": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "segsalsa_str_destroy": (None, [vp]),
+        "segsalsa_str_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor of `dtype`."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    # torch tensor
+    import torch
+    tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}
+    if a.dtype != tmap[np.dtype(dtype).type]:
+        raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), int(a.is_cuda)
+
+
+def _check(lib, h, rc):
+    if rc != SEGSALSA_OK:
+        msg = lib.segsalsa_str_last_error(h).decode()
+        raise SegsalsaError(rc, msg)
+
+
+# ------------------------------------------------------------------ C-ABI-named functions
+
+def segsalsa_str_workspace_bytes(params: Params) -> int:
+    lib = load()
+    n = C.c_size_t(0)
+    _check(lib, None, lib.segsalsa_str_workspace_bytes(C.byref(params), C.byref(n)))
+    return n.value
+
+
+def segsalsa_str_create(params: Params, workspace_ptr: int | None = None, workspace_bytes: int = 0):
+    lib = load()
+    h = C.c_void_p()
+    _check(lib, None, lib.segsalsa_str_create(C.byref(params), workspace_ptr, workspace_bytes,
+                                              C.byref(h)))
+    return h
+
+
+def segsalsa_str_destroy(h):
+    load().segsalsa_str_destroy(h)
+
+
+def segsalsa_str_last_error(h=None) -> str:
+    return load().segsalsa_str_last_error(h).decode()
+
+
+def make_params(H, W, K, M=1, sigma=0.5, lam=1.5, mu=1.0, schatten_p=1, precision="fp32",
+                weights=None, stream=None) -> Params:
+    pr = Params()
+    pr.H, pr.W, pr.K, pr.M = int(H), int(W), int(K), int(M)
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        pr._weights_keep = w
+        pr.weights = w.ctypes.data_as(C.POINTER(C.c_double))
+    else:
+        pr.weights = None
+    pr.sigma = float(sigma)
+    pr.lambda_ = float(lam)
+    pr.mu = float(mu)
+    sp = schatten_p
+    pr.schatten_p = SEGSALSA_SCHATTEN_INF if sp in (np.inf, float("inf"), "inf", 0) else int(sp)
+    pr.precision = SEGSALSA_FP64 if precision in ("fp64", np.float64, SEGSALSA_FP64) else SEGSALSA_FP32
+    pr.stream = stream
+    return pr
+
+
+class Solver:
+    """One solver handle (wraps segsalsa_str_*). Arrays: numpy (host) or torch (device)."""
+
+    def __init__(self, params: Params, workspace=None):
+        self.lib = load()
+        self.params = params
+        self.dtype = np.float64 if params.precision == SEGSALSA_FP64 else np.float32
+        self.H, self.W, self.K, self.M = params.H, params.W, params.K, params.M
+        self.L = (2 * self.M + 1) ** 2
+        self._ws = workspace  # keep the caller's memory alive
+        ptr, nbytes = (None, 0)
+        if workspace is not None:
+            ptr, nbytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+        self.h = segsalsa_str_create(params, ptr, nbytes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.segsalsa_str_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        _check(self.lib, self.h, rc)
+
+    # segsalsa_str_set_probs
+    def set_probs(self, p, layout=SEGSALSA_LAYOUT_KHW):
+        ptr, dev = _ptr(p, self.dtype)
+        self._c(self.lib.segsalsa_str_set_probs(self.h, ptr, layout, dev))
+
+    # segsalsa_str_solve
+    def solve(self, iters, trace_every=0):
+        if trace_every:
+            cap = iters // trace_every + 2
+            tr = np.zeros((cap, 6), dtype=np.float64)
+            n = C.c_int32(0)
+            self._c(self.lib.segsalsa_str_solve(
+                self.h, int(iters), tr.ctypes.data_as(C.POINTER(C.c_double)), int(trace_every),
+                C.byref(n)))
+            return tr[: n.value]
+        self._c(self.lib.segsalsa_str_solve(self.h, int(iters), None, 0, None))
+        return None
+
+    # segsalsa_str_get_labels
+    def get_labels(self, out=None):
+        if out is None:
+            out = np.empty((self.H, self.W), dtype=np.int32)
+        ptr, dev = _ptr(out, np.int32)
+        self._c(self.lib.segsalsa_str_get_labels(self.h, ptr, dev))
+        return out
+
+    # segsalsa_str_get_z
+    def get_z(self, out=None, layout=SEGSALSA_LAYOUT_KHW):
+        if out is None:
+            shape = (self.K, self.H, self.W) if layout == SEGSALSA_LAYOUT_KHW else (self.H, self.W, self.K)
+            out = np.empty(shape, dtype=self.dtype)
+        ptr, dev = _ptr(out, self.dtype)
+        self._c(self.lib.segsalsa_str_get_z(self.h, ptr, layout, dev))
+        return out
+
+    def get_iteration(self) -> int:
+        k = C.c_int32(0)
+        self._c(self.lib.segsalsa_str_get_iteration(self.h, C.byref(k)))
+        return k.value
+
+    def state_shapes(self):
+        H, W, K, L = self.H, self.W, self.K, self.L
+        return {"z": (H, W, K), "d1": (H, W, K), "d2": (H, W, L, K, 2), "d3": (H, W, K),
+                "d4": (H, W, K), "rhs": (H, W, K)}
+
+    # segsalsa_str_get_state
+    def get_state(self):
+        sh = self.state_shapes()
+        out = {k: np.empty(v, dtype=self.dtype) for k, v in sh.items()}
+        ptrs = [_ptr(out[k], self.dtype)[0] for k in ("z", "d1", "d2", "d3", "d4", "rhs")]
+        self._c(self.lib.segsalsa_str_get_state(self.h, *ptrs, 0))
+        return out
+
+    # segsalsa_str_set_state
+    def set_state(self, st: dict, k: int):
+        arrs = [np.ascontiguousarray(st[n], dtype=self.dtype) if st.get(n) is not None else None
+                for n in ("z", "d1", "d2", "d3", "d4", "rhs")]
+        ptrs = [_ptr(a, self.dtype)[0] for a in arrs]
+        self._c(self.lib.segsalsa_str_set_state(self.h, *ptrs, int(k), 0))
+
+    # segsalsa_str_linear_solve
+    def linear_solve(self, rhs, out=None):
+        if out is None:
+            out = np.empty_like(rhs) if isinstance(rhs, np.ndarray) else rhs.new_empty(rhs.shape)
+        p1, d1 = _ptr(rhs, self.dtype)
+        p2, d2 = _ptr(out, self.dtype)
+        if d1 != d2:
+            raise ValueError("rhs and z must both be host or both be device arrays")
+        self._c(self.lib.segsalsa_str_linear_solve(self.h, p1, p2, d1))
+        return out
+
+    def set_profiling(self, on: bool):
+        self._c(self.lib.segsalsa_str_set_profiling(self.h, int(bool(on))))
+
+    def kernel_stats(self):
+        n = (C.c_int64 * 6)()
+        ms = (C.c_double * 6)()
+        self._c(self.lib.segsalsa_str_kernel_stats(self.h, n, ms))
+        return {KERNEL_KINDS[i]: (int(n[i]), float(ms[i])) for i in range(6)}
+
+    def reset_stats(self):
+        self._c(self.lib.segsalsa_str_reset_stats(self.h))
+
+    def traffic_model(self):
+        a, b = C.c_double(0), C.c_double(0)
+        self._c(self.lib.segsalsa_str_traffic_model(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value

@@ -1,0 +1,800 @@
+// Host side of the SegSALSA-STR library: planning, workspace, iteration loop, C ABI.
+//
+// One iteration of SALSA (eqs. 12-14) is, in launch order,
+//   [k > 0]  row FFT forward (gathers rhs^k from the sweep's tile partials) -> column solve
+//            -> row FFT inverse: z^{k+1} = (3 I + J^T J)^{-1} G^T (u^k + d^k)       (eq. 12)
+//   sweep:   u^{k+1}, d^{k+1} and the tile partials of rhs^{k+1}                  (eqs. 13-14)
+// For k = 0 the z-update is the identity (u^0 = G z^0, d^0 = 0), so it is skipped.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/segsalsa_str.h"
+#include "aux.cuh"
+#include "fft.cuh"
+#include "launch.h"
+
+namespace sgs {
+
+enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIAG = 4, KIND_OTHER = 5 };
+constexpr int NKIND = 6;
+constexpr int MAXCOV = 2;           // tile covers per row / column in the partial gather
+constexpr int TRACE_CAP = 128;      // device trace records before a flush to the host
+
+static thread_local std::string g_last_error;
+
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static bool is_smooth7(long n) {
+  for (long r : {2L, 3L, 5L, 7L})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
+static std::vector<int> radices_of(int m) {
+  std::vector<int> r;
+  while (m % 8 == 0) { r.push_back(8); m /= 8; }
+  while (m % 4 == 0) { r.push_back(4); m /= 4; }
+  while (m % 2 == 0) { r.push_back(2); m /= 2; }
+  for (int p : {3, 5, 7})
+    while (m % p == 0) { r.push_back(p); m /= p; }
+  return r;
+}
+
+struct SolverBase {
+  virtual ~SolverBase() {}
+  std::string err;
+  virtual int set_probs(const void* p, int layout, int on_device) = 0;
+  virtual int solve(int iters, double* trace, int every, int* nrec) = 0;
+  virtual int get_labels(int32_t* lab, int on_device) = 0;
+  virtual int get_z(void* z, int layout, int on_device) = 0;
+  virtual int get_iteration(int* k) const = 0;
+  virtual int get_state(void* z, void* d1, void* d2, void* d3, void* d4, void* rhs, int dev) = 0;
+  virtual int set_state(const void* z, const void* d1, const void* d2, const void* d3,
+                        const void* d4, const void* rhs, int k, int dev) = 0;
+  virtual int linear_solve(const void* rhs, void* z, int dev) = 0;
+  virtual int set_profiling(int on) = 0;
+  virtual int kernel_stats(int64_t* launches, double* ms) = 0;
+  virtual int reset_stats() = 0;
+  virtual int traffic(double* sweep, double* iter) const = 0;
+  int fail(int code, const std::string& m) { err = m; return code; }
+};
+
+// Validation of the parameters shared by create and workspace_bytes.
+static int check_params(const segsalsa_str_params* pr, std::string& msg) {
+  if (!pr) { msg = "params is NULL"; return SEGSALSA_ERR_ARG; }
+  if (pr->M < 0 || pr->M > 2) { msg = "M must be 0, 1 or 2"; return SEGSALSA_ERR_ARG; }
+  if (pr->K < 2 || pr->K > 32) { msg = "K must be in [2, 32]"; return SEGSALSA_ERR_ARG; }
+  const int minsz = 2 * pr->M + 2;
+  if (pr->H < minsz || pr->W < minsz) { msg = "H and W must be >= 2M+2"; return SEGSALSA_ERR_ARG; }
+  if ((long long)pr->H * pr->W > (1LL << 30)) { msg = "image too large"; return SEGSALSA_ERR_ARG; }
+  if (pr->H > 65535 || pr->W > 65535) { msg = "H and W must be <= 65535"; return SEGSALSA_ERR_ARG; }
+  if (!(pr->lambda >= 0.0) || !std::isfinite(pr->lambda)) { msg = "lambda must be finite and >= 0"; return SEGSALSA_ERR_ARG; }
+  if (!(pr->mu > 0.0) || !std::isfinite(pr->mu)) { msg = "mu must be finite and > 0"; return SEGSALSA_ERR_ARG; }
+  if (pr->schatten_p != 1 && pr->schatten_p != 2 && pr->schatten_p != SEGSALSA_SCHATTEN_INF) {
+    msg = "schatten_p must be 1, 2 or SEGSALSA_SCHATTEN_INF"; return SEGSALSA_ERR_ARG;
+  }
+  if (pr->precision != SEGSALSA_FP32 && pr->precision != SEGSALSA_FP64) {
+    msg = "precision must be SEGSALSA_FP32 or SEGSALSA_FP64"; return SEGSALSA_ERR_ARG;
+  }
+  const int L = (2 * pr->M + 1) * (2 * pr->M + 1);
+  if (pr->weights) {
+    for (int j = 0; j < L; ++j)
+      if (!std::isfinite(pr->weights[j])) { msg = "weights must be finite"; return SEGSALSA_ERR_ARG; }
+  } else if (!(pr->sigma > 0.0) || !std::isfinite(pr->sigma)) {
+    msg = "sigma must be finite and > 0 when weights is NULL"; return SEGSALSA_ERR_ARG;
+  }
+  return SEGSALSA_OK;
+}
+
+// Shift weights: given, or omega_j = sqrt(normalised Gaussian) (the weighted shifts of Sec. 3).
+static std::vector<double> make_weights(const segsalsa_str_params* pr) {
+  const int M = pr->M, P = 2 * M + 1;
+  std::vector<double> w(P * P);
+  if (pr->weights) {
+    for (int j = 0; j < P * P; ++j) w[j] = pr->weights[j];
+    return w;
+  }
+  double s = 0.0;
+  for (int dy = -M; dy <= M; ++dy)
+    for (int dx = -M; dx <= M; ++dx) {
+      const double g = std::exp(-(double)(dy * dy + dx * dx) / (2.0 * pr->sigma * pr->sigma));
+      w[(dy + M) * P + dx + M] = g;
+      s += g;
+    }
+  for (auto& v : w) v = std::sqrt(v / s);
+  return w;
+}
+
+// Everything decided from the parameters before memory exists.
+struct Plan {
+  int H, W, K, M, L, n, G, NC;
+  int ntx, nty, THmax, EHmax, EWmax, ntiles;
+  size_t sweep_smem, sweep_smem_diag;
+  int Wh, Mf, blue, QB, row_threads, nqblk;
+  std::vector<int> radix;
+  size_t row_smem;
+  int CB, NSEG, col_threads, ncolblk;
+  size_t col_smem;
+  int nproj_blk, nprior_blk, ngsq_blk;
+  std::vector<int> covY, covX;  // [H][MAXCOV], [W][MAXCOV]
+};
+
+static bool build_cover(int N, int ntile, int lo, int hi, std::vector<int>& cov) {
+  cov.assign((size_t)N * MAXCOV, -1);
+  std::vector<int> cnt(N, 0);
+  for (int t = 0; t < ntile; ++t) {
+    const int a = (int)(((long long)t * N) / ntile), b = (int)(((long long)(t + 1) * N) / ntile);
+    const int ext = (b - a) + lo + hi;
+    for (int e = 0; e < ext; ++e) {
+      const int x = wrap_idx(a - lo + e, N);
+      if (cnt[x] >= MAXCOV) return false;
+      cov[(size_t)x * MAXCOV + cnt[x]++] = (t << 16) | e;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) {
+  pl.H = pr->H; pl.W = pr->W; pl.K = pr->K; pl.M = pr->M;
+  pl.L = (2 * pl.M + 1) * (2 * pl.M + 1);
+  pl.n = pl.H * pl.W;
+  const int K = pl.K, M = pl.M, H = pl.H, W = pl.W;
+  pl.G = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  pl.NC = 256 / pl.G;
+  pl.ntx = (W + pl.NC - 1) / pl.NC;
+  // tile height: the largest of {16, 12, 8, 6, 4} that still gives two CTAs per SM (152 SMs);
+  // with more than one tile row every tile must be at least 2M+1 rows high
+  const int cand[] = {16, 12, 8, 6, 4};
+  pl.THmax = 0;
+  int fallback = 0;
+  for (int th : cand) {
+    const int nty = (H + th - 1) / th;
+    if (nty > 1 && H / nty < 2 * M + 1) continue;
+    fallback = th;
+    if ((long long)nty * pl.ntx >= 304) { pl.THmax = th; break; }
+  }
+  if (!pl.THmax) pl.THmax = fallback ? fallback : H;
+  pl.nty = (H + pl.THmax - 1) / pl.THmax;
+  pl.EHmax = pl.THmax + 2 * M + 1;
+  pl.EWmax = pl.NC + 2 * M + 1;
+  pl.sweep_smem = sweep_smem_bytes<T>(pl.EHmax, pl.EWmax, pl.G, pl.L, false);
+  pl.sweep_smem_diag = sweep_smem_bytes<T>(pl.EHmax, pl.EWmax, pl.G, pl.L, true);
+  if (pl.sweep_smem_diag > 220 * 1024) { msg = "tile does not fit in shared memory"; return SEGSALSA_ERR_ARG; }
+  pl.ntiles = pl.ntx * pl.nty;
+  if (!build_cover(H, pl.nty, M, M + 1, pl.covY) || !build_cover(W, pl.ntx, M, M + 1, pl.covX)) {
+    msg = "image too small for the tiling"; return SEGSALSA_ERR_ARG;
+  }
+  // row FFT
+  pl.Wh = W / 2 + 1;
+  if (is_smooth7(W)) { pl.Mf = W; pl.blue = 0; }
+  else {
+    pl.blue = 1;
+    long m = 2L * W - 1;
+    while (!is_smooth7(m)) ++m;
+    pl.Mf = (int)m;
+  }
+  if (pl.Mf > 16 * 512) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
+  pl.radix = radices_of(pl.Mf);
+  if ((int)pl.radix.size() > FFT_MAXST) { msg = "too many FFT stages"; return SEGSALSA_ERR_ARG; }
+  const int Q = (K + 1) / 2;
+  pl.QB = std::max(1, std::min(Q, (16 * 512) / pl.Mf));
+  pl.nqblk = (Q + pl.QB - 1) / pl.QB;
+  pl.QB = (Q + pl.nqblk - 1) / pl.nqblk;  // balance the pair chunks
+  const int need = (pl.Mf * pl.QB + FFT_MAXE - 1) / FFT_MAXE;
+  pl.row_threads = std::min(512, std::max(64, (need + 31) / 32 * 32));
+  pl.row_smem = sizeof(cplx<T>) * (size_t)pl.Mf * pl.QB;
+  // column solve
+  pl.CB = sizeof(T) == 4 ? 8 : 4;
+  while ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024 && pl.CB > 1) pl.CB /= 2;
+  if ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024) { msg = "image too tall for the column solve"; return SEGSALSA_ERR_ARG; }
+  pl.col_smem = (size_t)H * pl.CB * sizeof(cplx<T>);
+  const int nseq = 2 * pl.CB;
+  pl.NSEG = std::max(1, std::min(H / 24, 1024 / nseq));
+  pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
+  pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
+  // diagnostics
+  const int cap = 152 * 8;
+  pl.nproj_blk = std::min(cap, (pl.n + AUX_THREADS - 1) / AUX_THREADS);
+  pl.nprior_blk = pl.nproj_blk;
+  pl.ngsq_blk = (int)std::min<long long>(cap, ((long long)pl.n * K + AUX_THREADS - 1) / AUX_THREADS);
+  return SEGSALSA_OK;
+}
+
+// Carves the workspace (dry run: only sizes).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class U> U* take(size_t count) {
+    off = align_up(off, 256);
+    U* p = base ? reinterpret_cast<U*>(base + off) : nullptr;
+    off += count * sizeof(U);
+    return p;
+  }
+};
+
+template <typename T>
+struct Buffers {
+  T *p, *z, *dloc, *d2, *P, *P2, *zp, *tmp, *rhsd;
+  cplx<T>* S;
+  int32_t* lab;
+  double *dsq, *dproj, *dprior, *dgsq, *dtrace;
+  int* flag;
+  T* omega;
+  int *covY, *covX;
+  T *beta, *gain, *wfac;
+  int* nwarm;
+  cplx<T>*tw, *chirp, *bhat;
+};
+
+template <typename T>
+static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
+  Carver c{base};
+  const size_t nK = (size_t)pl.n * pl.K;
+  b.p = c.take<T>(nK);
+  b.z = c.take<T>(nK);
+  b.dloc = c.take<T>(3 * nK);
+  b.d2 = c.take<T>(2 * (size_t)pl.L * nK);
+  const size_t tslot = (size_t)pl.ntiles * pl.EHmax * pl.EWmax * pl.K;
+  b.P = c.take<T>(tslot);
+  b.P2 = c.take<T>(tslot);
+  b.zp = c.take<T>(nK);
+  b.tmp = c.take<T>(nK);
+  b.rhsd = c.take<T>(nK);
+  b.S = c.take<cplx<T>>((size_t)pl.H * pl.Wh * pl.K);
+  b.lab = c.take<int32_t>(pl.n);
+  b.dsq = c.take<double>(pl.ntiles);
+  b.dproj = c.take<double>(3 * (size_t)pl.nproj_blk);
+  b.dprior = c.take<double>(pl.nprior_blk);
+  b.dgsq = c.take<double>(pl.ngsq_blk);
+  b.dtrace = c.take<double>(6 * (size_t)TRACE_CAP);
+  b.flag = c.take<int>(1);
+  b.omega = c.take<T>(pl.L);
+  b.covY = c.take<int>((size_t)pl.H * MAXCOV);
+  b.covX = c.take<int>((size_t)pl.W * MAXCOV);
+  b.beta = c.take<T>(pl.Wh);
+  b.gain = c.take<T>(pl.Wh);
+  b.wfac = c.take<T>(pl.Wh);
+  b.nwarm = c.take<int>(pl.Wh);
+  b.tw = c.take<cplx<T>>(pl.Mf);
+  b.chirp = c.take<cplx<T>>(pl.W);
+  b.bhat = c.take<cplx<T>>(pl.Mf);
+  return align_up(c.off, 256);
+}
+
+#define SGS_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(SEGSALSA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <typename T>
+class Solver : public SolverBase {
+ public:
+  Plan pl;
+  Buffers<T> b{};
+  std::vector<double> omega;
+  double lambda = 0, mu = 1, c_omega = 0;
+  int sp = 1;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  void* ws = nullptr;
+  bool own_ws = false;
+  int iter = 0;
+  bool have_probs = false;
+  bool rhs_dense = false;  // next z-update reads b.rhsd instead of the partials
+  int64_t nlaunch[NKIND] = {0};
+  double ms[NKIND] = {0};
+  bool profiling = false;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> evs;
+  std::vector<cudaEvent_t> evpool;
+
+  ~Solver() override {
+    if (st) cudaStreamSynchronize(st);
+    for (auto& e : evs) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
+    for (auto e : evpool) cudaEventDestroy(e);
+    if (own_ws && ws) cudaFree(ws);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+
+  int init(const segsalsa_str_params* pr, void* workspace, size_t wsbytes) {
+    std::string msg;
+    int rc = make_plan<T>(pr, pl, msg);
+    if (rc) return fail(rc, msg);
+    omega = make_weights(pr);
+    lambda = pr->lambda;
+    mu = pr->mu;
+    sp = pr->schatten_p == SEGSALSA_SCHATTEN_INF ? 0 : pr->schatten_p;
+    c_omega = 0.0;
+    for (double w : omega) c_omega += w * w;
+    const size_t need = carve<T>(pl, nullptr, b);
+    if (workspace) {
+      if (wsbytes < need) return fail(SEGSALSA_ERR_OOM, "workspace too small");
+      if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(SEGSALSA_ERR_ARG, "workspace must be 256-byte aligned");
+      ws = workspace;
+    } else {
+      cudaError_t e = cudaMalloc(&ws, need);
+      if (e != cudaSuccess) { ws = nullptr; return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+      own_ws = true;
+    }
+    carve<T>(pl, reinterpret_cast<char*>(ws), b);
+    if (pr->stream) st = reinterpret_cast<cudaStream_t>(pr->stream);
+    else { SGS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+    return upload_tables();
+  }
+
+  int upload_tables() {
+    const int H = pl.H, W = pl.W, Wh = pl.Wh, Mf = pl.Mf;
+    std::vector<T> om(pl.L);
+    for (int j = 0; j < pl.L; ++j) om[j] = (T)omega[j];
+    SGS_CUDA(cudaMemcpyAsync(b.omega, om.data(), sizeof(T) * pl.L, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.covY, pl.covY.data(), sizeof(int) * pl.covY.size(), cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.covX, pl.covX.data(), sizeof(int) * pl.covX.size(), cudaMemcpyHostToDevice, st));
+    // column solve coefficients, per kx: (a + 2c) - c (S + S^-1) = (c/beta)(1 - beta S)(1 - beta/S)
+    std::vector<T> beta(Wh), gain(Wh), wfac(Wh);
+    std::vector<int> nwarm(Wh);
+    const double tol = sizeof(T) == 4 ? 1e-9 : 1e-18;
+    const double c = c_omega;
+    for (int kx = 0; kx < Wh; ++kx) {
+      const double s = std::sin(M_PI * kx / W);
+      const double alpha = 3.0 + c * (4.0 * s * s + 2.0);
+      if (c > 0.0) {
+        const double t = alpha / c;
+        const double bt = 2.0 / (t + std::sqrt(t * t - 4.0));
+        const double gn = 2.0 / (alpha + std::sqrt(alpha * alpha - 4.0 * c * c));
+        int nw = (int)std::ceil(std::log(tol * (1.0 - bt)) / std::log(bt));
+        double wf = 1.0;
+        if (nw >= H || nw < 0) { nw = H; wf = 1.0 / (1.0 - std::pow(bt, H)); }
+        beta[kx] = (T)bt; gain[kx] = (T)gn; wfac[kx] = (T)wf; nwarm[kx] = nw;
+      } else {
+        beta[kx] = 0; gain[kx] = (T)(1.0 / alpha); wfac[kx] = 1; nwarm[kx] = 0;
+      }
+    }
+    SGS_CUDA(cudaMemcpyAsync(b.beta, beta.data(), sizeof(T) * Wh, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.gain, gain.data(), sizeof(T) * Wh, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.wfac, wfac.data(), sizeof(T) * Wh, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.nwarm, nwarm.data(), sizeof(int) * Wh, cudaMemcpyHostToDevice, st));
+    // FFT tables (FP64 on the host)
+    std::vector<cplx<T>> tw(Mf), chirp(W), bhat(Mf);
+    for (int m = 0; m < Mf; ++m) {
+      const double ang = -2.0 * M_PI * (double)m / Mf;
+      tw[m] = mkc<T>((T)std::cos(ang), (T)std::sin(ang));
+    }
+    if (pl.blue) {
+      std::vector<std::complex<double>> ch(W), bb(Mf, 0.0), twd(Mf);
+      for (int m = 0; m < W; ++m) {
+        const long long q = ((long long)m * m) % (2LL * W);
+        const double ang = M_PI * (double)q / W;
+        ch[m] = std::complex<double>(std::cos(ang), std::sin(ang));
+        chirp[m] = mkc<T>((T)ch[m].real(), (T)ch[m].imag());
+      }
+      for (int m = 0; m < W; ++m) bb[m] = ch[m];
+      for (int m = 1; m < W; ++m) bb[Mf - m] = ch[m];
+      for (int m = 0; m < Mf; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / Mf;
+        twd[m] = std::complex<double>(std::cos(ang), std::sin(ang));
+      }
+      for (int k = 0; k < Mf; ++k) {
+        std::complex<double> acc = 0.0;
+        for (int m = 0; m < Mf; ++m) acc += bb[m] * twd[((long long)k * m) % Mf];
+        acc /= (double)Mf;
+        bhat[k] = mkc<T>((T)acc.real(), (T)acc.imag());
+      }
+    } else {
+      for (int m = 0; m < W; ++m) chirp[m] = mkc<T>(T(1), T(0));
+      for (int m = 0; m < Mf; ++m) bhat[m] = mkc<T>(T(1), T(0));
+    }
+    SGS_CUDA(cudaMemcpyAsync(b.tw, tw.data(), sizeof(cplx<T>) * Mf, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.chirp, chirp.data(), sizeof(cplx<T>) * W, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemcpyAsync(b.bhat, bhat.data(), sizeof(cplx<T>) * Mf, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    return SEGSALSA_OK;
+  }
+
+  // ---------------------------------------------------------------- launch bookkeeping
+  cudaEvent_t get_event() {
+    if (!evpool.empty()) { cudaEvent_t e = evpool.back(); evpool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  template <class F> cudaError_t launch(int kind, F&& f) {
+    nlaunch[kind]++;
+    if (!profiling) return f();
+    cudaEvent_t a = get_event(), c = get_event();
+    cudaEventRecord(a, st);
+    cudaError_t e = f();
+    cudaEventRecord(c, st);
+    evs.emplace_back(kind, a, c);
+    return e;
+  }
+#define SGS_LAUNCH(kind, expr) SGS_CUDA(launch(kind, [&]() -> cudaError_t { expr; return cudaGetLastError(); }))
+
+  FftPlan<T> fft_plan() const {
+    FftPlan<T> f{};
+    f.N = pl.W; f.Mf = pl.Mf; f.blue = pl.blue; f.nst = (int)pl.radix.size();
+    int ns = 1;
+    for (int s = 0; s < f.nst; ++s) { f.radix[s] = pl.radix[s]; f.ns[s] = ns; ns *= pl.radix[s]; }
+    f.tw = b.tw; f.chirp = b.chirp; f.bhat = b.bhat;
+    return f;
+  }
+  RowArgs<T> row_args(const T* src, T* zout) const {
+    RowArgs<T> a{};
+    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.Wh = pl.Wh; a.QB = pl.QB;
+    a.pl = fft_plan();
+    a.src = src; a.P = b.P; a.ntx = pl.ntx; a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
+    a.covY = b.covY; a.covX = b.covX; a.S = b.S; a.z = zout;
+    return a;
+  }
+
+  // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep partials (src == nullptr)
+  int z_update(const T* src, T* zout) {
+    const RowArgs<T> ra = row_args(src, zout);
+    const dim3 rg(pl.H, pl.nqblk);
+    SGS_CUDA(cudaFuncSetAttribute(k_row_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.row_smem));
+    SGS_CUDA(cudaFuncSetAttribute(k_row_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.row_smem));
+    SGS_CUDA(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.col_smem));
+    SGS_LAUNCH(KIND_ROWF, (k_row_forward<T><<<rg, pl.row_threads, pl.row_smem, st>>>(ra)));
+    ColArgs<T> ca{};
+    ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG;
+    ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
+    SGS_LAUNCH(KIND_COL, (k_col_solve<T><<<pl.ncolblk, pl.col_threads, pl.col_smem, st>>>(ca)));
+    SGS_LAUNCH(KIND_ROWI, (k_row_inverse<T><<<rg, pl.row_threads, pl.row_smem, st>>>(ra)));
+    return SEGSALSA_OK;
+  }
+
+  int sweep(bool diag) {
+    SweepArgs<T> a{};
+    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.ntx = pl.ntx; a.nty = pl.nty;
+    a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
+    a.z = b.z; a.p = b.p; a.dloc = b.dloc; a.d2 = b.d2; a.P = b.P; a.P2 = b.P2;
+    a.diag_sq = b.dsq; a.omega = b.omega;
+    a.tau = (T)(lambda / mu); a.mu = (T)mu; a.invK = (T)(1.0 / pl.K); a.sp = sp;
+    const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
+    SGS_CUDA(launch(KIND_SWEEP, [&]() { return launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st); }));
+    return SEGSALSA_OK;
+  }
+
+  int diagnostics(int k, int rec) {
+    const int n = pl.n, K = pl.K;
+    SGS_LAUNCH(KIND_DIAG, (k_project<T><<<pl.nproj_blk, AUX_THREADS, 0, st>>>(b.z, b.p, b.zp, n, K, b.dproj)));
+    SGS_LAUNCH(KIND_DIAG, (k_prior<T><<<pl.nprior_blk, AUX_THREADS, 0, st>>>(b.zp, b.omega, pl.H, pl.W, K, pl.M, sp, b.dprior)));
+    SGS_LAUNCH(KIND_DIAG, (k_gather_sq<T><<<pl.ngsq_blk, AUX_THREADS, 0, st>>>(b.P2, b.covY, b.covX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq)));
+    SGS_LAUNCH(KIND_DIAG, (k_finalize_trace<<<1, 256, 0, st>>>(b.dsq, pl.ntiles, b.dgsq, pl.ngsq_blk, b.dproj, pl.nproj_blk, b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec)));
+    return SEGSALSA_OK;
+  }
+
+  int flush_trace(int count, double* host, int& written) {
+    if (count <= 0) return SEGSALSA_OK;
+    SGS_CUDA(cudaMemcpyAsync(host + 6 * (size_t)written, b.dtrace, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    written += count;
+    return SEGSALSA_OK;
+  }
+
+  // ---------------------------------------------------------------------- API methods
+  int copy_in(T* dst, const void* src, size_t count, int dev) {
+    SGS_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return SEGSALSA_OK;
+  }
+  int copy_out(void* dst, const T* src, size_t count, int dev) {
+    SGS_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return SEGSALSA_OK;
+  }
+  int grid1(size_t count) const { return (int)((count + AUX_THREADS - 1) / AUX_THREADS); }
+
+  int set_probs(const void* p, int layout, int dev) override {
+    if (!p) return fail(SEGSALSA_ERR_ARG, "p is NULL");
+    if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
+    const int n = pl.n, K = pl.K;
+    const size_t nK = (size_t)n * K;
+    int rc;
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_in(b.tmp, p, nK, dev))) return rc;
+    } else {
+      if ((rc = copy_in(b.zp, p, nK, dev))) return rc;
+      SGS_LAUNCH(KIND_OTHER, (k_khw_to_hwk<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.zp, b.tmp, n, K)));
+    }
+    SGS_CUDA(cudaMemsetAsync(b.flag, 0, sizeof(int), st));
+    SGS_LAUNCH(KIND_OTHER, (k_check_probs<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.tmp, n, K, b.flag)));
+    int flag = 0;
+    SGS_CUDA(cudaMemcpyAsync(&flag, b.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    if (flag & 1) return fail(SEGSALSA_ERR_ARG, "p has non-finite entries");
+    if (flag & 2) return fail(SEGSALSA_ERR_ARG, "p has negative entries");
+    if (flag & 4) return fail(SEGSALSA_ERR_ARG, "p has a pixel without a positive entry");
+    SGS_CUDA(cudaMemcpyAsync(b.p, b.tmp, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st));
+    SGS_LAUNCH(KIND_OTHER, (k_init_z<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.p, b.z, n, K)));
+    SGS_CUDA(cudaMemsetAsync(b.dloc, 0, sizeof(T) * 3 * nK, st));
+    SGS_CUDA(cudaMemsetAsync(b.d2, 0, sizeof(T) * 2 * pl.L * nK, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    iter = 0;
+    rhs_dense = false;
+    have_probs = true;
+    return SEGSALSA_OK;
+  }
+
+  int solve(int iters, double* trace, int every, int* nrec) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "solve before set_probs");
+    if (iters < 0) return fail(SEGSALSA_ERR_ARG, "iters must be >= 0");
+    if (trace && every < 1) return fail(SEGSALSA_ERR_ARG, "trace_every must be >= 1");
+    int pending = 0, written = 0, rc;
+    for (int it = 0; it < iters; ++it) {
+      if (iter > 0) {
+        if ((rc = z_update(rhs_dense ? b.rhsd : nullptr, b.z))) return rc;
+        rhs_dense = false;
+      }
+      const bool tr = trace && (((iter + 1) % every) == 0 || it == iters - 1);
+      if ((rc = sweep(tr))) return rc;
+      if (tr) {
+        if ((rc = diagnostics(iter + 1, pending))) return rc;
+        if (++pending == TRACE_CAP) {
+          if ((rc = flush_trace(pending, trace, written))) return rc;
+          pending = 0;
+        }
+      }
+      ++iter;
+    }
+    if (trace && (rc = flush_trace(pending, trace, written))) return rc;
+    SGS_CUDA(cudaStreamSynchronize(st));
+    if (nrec) *nrec = written;
+    if (trace)
+      for (int i = 0; i < 6 * written; ++i)
+        if (!std::isfinite(trace[i])) return fail(SEGSALSA_ERR_NUMERIC, "non-finite value in the iterates");
+    return SEGSALSA_OK;
+  }
+
+  int get_labels(int32_t* lab, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "no state: call set_probs first");
+    if (!lab) return fail(SEGSALSA_ERR_ARG, "labels is NULL");
+    SGS_LAUNCH(KIND_OTHER, (k_labels<T><<<grid1(pl.n), AUX_THREADS, 0, st>>>(b.z, pl.n, pl.K, b.lab)));
+    SGS_CUDA(cudaMemcpyAsync(lab, b.lab, sizeof(int32_t) * pl.n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    return SEGSALSA_OK;
+  }
+
+  int get_z(void* z, int layout, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "no state: call set_probs first");
+    if (!z) return fail(SEGSALSA_ERR_ARG, "z is NULL");
+    if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_out(z, b.z, nK, dev))) return rc;
+    } else {
+      SGS_LAUNCH(KIND_OTHER, (k_hwk_to_khw<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.z, b.tmp, pl.n, pl.K)));
+      if ((rc = copy_out(z, b.tmp, nK, dev))) return rc;
+    }
+    SGS_CUDA(cudaStreamSynchronize(st));
+    return SEGSALSA_OK;
+  }
+
+  int get_iteration(int* k) const override {
+    if (!k) return SEGSALSA_ERR_ARG;
+    *k = iter;
+    return SEGSALSA_OK;
+  }
+
+  int get_state(void* z, void* d1, void* d2, void* d3, void* d4, void* rhs, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "no state: call set_probs first");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    if (z && (rc = copy_out(z, b.z, nK, dev))) return rc;
+    if (d2 && (rc = copy_out(d2, b.d2, 2 * pl.L * nK, dev))) return rc;
+    void* dl[3] = {d1, d3, d4};
+    for (int j = 0; j < 3; ++j) {
+      if (!dl[j]) continue;
+      // dloc is [n][3][K]: gather plane j
+      SGS_CUDA(cudaMemcpy2DAsync(b.tmp, sizeof(T) * pl.K, b.dloc + (size_t)j * pl.K, sizeof(T) * 3 * pl.K,
+                                 sizeof(T) * pl.K, pl.n, cudaMemcpyDeviceToDevice, st));
+      if ((rc = copy_out(dl[j], b.tmp, nK, dev))) return rc;
+      SGS_CUDA(cudaStreamSynchronize(st));
+    }
+    if (rhs) {
+      if (rhs_dense) {
+        if ((rc = copy_out(rhs, b.rhsd, nK, dev))) return rc;
+      } else {
+        const RowArgs<T> ra = row_args(nullptr, b.tmp);
+        SGS_LAUNCH(KIND_OTHER, (k_gather_dense<T><<<grid1(nK), AUX_THREADS, 0, st>>>(ra)));
+        if ((rc = copy_out(rhs, b.tmp, nK, dev))) return rc;
+      }
+    }
+    SGS_CUDA(cudaStreamSynchronize(st));
+    return SEGSALSA_OK;
+  }
+
+  int set_state(const void* z, const void* d1, const void* d2, const void* d3, const void* d4,
+                const void* rhs, int k, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "set_probs must come first (p is kept)");
+    if (!z || !d1 || !d2 || !d3 || !d4) return fail(SEGSALSA_ERR_ARG, "z, d1..d4 are required");
+    if (k < 0) return fail(SEGSALSA_ERR_ARG, "k must be >= 0");
+    if (k > 0 && !rhs) return fail(SEGSALSA_ERR_ARG, "rhs is required when k > 0");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    if ((rc = copy_in(b.z, z, nK, dev))) return rc;
+    if ((rc = copy_in(b.d2, d2, 2 * pl.L * nK, dev))) return rc;
+    const void* dl[3] = {d1, d3, d4};
+    for (int j = 0; j < 3; ++j) {
+      if ((rc = copy_in(b.tmp, dl[j], nK, dev))) return rc;
+      SGS_CUDA(cudaMemcpy2DAsync(b.dloc + (size_t)j * pl.K, sizeof(T) * 3 * pl.K, b.tmp, sizeof(T) * pl.K,
+                                 sizeof(T) * pl.K, pl.n, cudaMemcpyDeviceToDevice, st));
+    }
+    if (k > 0) {
+      if ((rc = copy_in(b.rhsd, rhs, nK, dev))) return rc;
+      rhs_dense = true;
+    } else {
+      rhs_dense = false;
+    }
+    SGS_CUDA(cudaStreamSynchronize(st));
+    iter = k;
+    return SEGSALSA_OK;
+  }
+
+  int linear_solve(const void* rhs, void* z, int dev) override {
+    if (!rhs || !z) return fail(SEGSALSA_ERR_ARG, "rhs and z are required");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    const T* src = reinterpret_cast<const T*>(rhs);
+    if (!dev) {
+      if ((rc = copy_in(b.tmp, rhs, nK, 0))) return rc;
+      src = b.tmp;
+    }
+    T* out = dev ? reinterpret_cast<T*>(z) : b.zp;
+    if ((rc = z_update(src, out))) return rc;
+    if (!dev && (rc = copy_out(z, b.zp, nK, 0))) return rc;
+    SGS_CUDA(cudaStreamSynchronize(st));
+    return SEGSALSA_OK;
+  }
+
+  int set_profiling(int on) override {
+    profiling = on != 0;
+    return SEGSALSA_OK;
+  }
+  int kernel_stats(int64_t* launches, double* msout) override {
+    if (!launches) return fail(SEGSALSA_ERR_ARG, "launches is NULL");
+    SGS_CUDA(cudaStreamSynchronize(st));
+    for (auto& e : evs) {
+      float t = 0.f;
+      SGS_CUDA(cudaEventElapsedTime(&t, std::get<1>(e), std::get<2>(e)));
+      ms[std::get<0>(e)] += t;
+      evpool.push_back(std::get<1>(e));
+      evpool.push_back(std::get<2>(e));
+    }
+    evs.clear();
+    for (int i = 0; i < NKIND; ++i) {
+      launches[i] = nlaunch[i];
+      if (msout) msout[i] = ms[i];
+    }
+    return SEGSALSA_OK;
+  }
+  int reset_stats() override {
+    int64_t tmpl[NKIND];
+    int rc = kernel_stats(tmpl, nullptr);
+    if (rc) return rc;
+    for (int i = 0; i < NKIND; ++i) { nlaunch[i] = 0; ms[i] = 0; }
+    return SEGSALSA_OK;
+  }
+  int traffic(double* sw, double* it) const override {
+    const double unit = (double)sizeof(T) * pl.n * pl.K;
+    if (sw) *sw = unit * (4.0 * pl.L + 9.0);
+    if (it) *it = unit * (4.0 * pl.L + 11.0);
+    return SEGSALSA_OK;
+  }
+};
+
+static int create_any(const segsalsa_str_params* pr, void* ws, size_t wsb,
+                      std::unique_ptr<SolverBase>& out, std::string& msg) {
+  int rc = check_params(pr, msg);
+  if (rc) return rc;
+  if (pr->precision == SEGSALSA_FP32) {
+    auto s = std::make_unique<Solver<float>>();
+    rc = s->init(pr, ws, wsb);
+    if (rc) { msg = s->err; return rc; }
+    out = std::move(s);
+  } else {
+    auto s = std::make_unique<Solver<double>>();
+    rc = s->init(pr, ws, wsb);
+    if (rc) { msg = s->err; return rc; }
+    out = std::move(s);
+  }
+  return SEGSALSA_OK;
+}
+
+}  // namespace sgs
+
+struct segsalsa_str {
+  std::unique_ptr<sgs::SolverBase> impl;
+};
+
+extern "C" {
+
+int segsalsa_str_workspace_bytes(const segsalsa_str_params* pr, size_t* bytes) {
+  std::string msg;
+  int rc = sgs::check_params(pr, msg);
+  if (!rc && !bytes) { rc = SEGSALSA_ERR_ARG; msg = "bytes is NULL"; }
+  if (!rc) {
+    sgs::Plan pl;
+    if (pr->precision == SEGSALSA_FP32) {
+      rc = sgs::make_plan<float>(pr, pl, msg);
+      sgs::Buffers<float> b{};
+      if (!rc) *bytes = sgs::carve<float>(pl, nullptr, b);
+    } else {
+      rc = sgs::make_plan<double>(pr, pl, msg);
+      sgs::Buffers<double> b{};
+      if (!rc) *bytes = sgs::carve<double>(pl, nullptr, b);
+    }
+  }
+  if (rc) sgs::g_last_error = msg;
+  return rc;
+}
+
+int segsalsa_str_create(const segsalsa_str_params* pr, void* ws, size_t wsb, segsalsa_str_t** out) {
+  if (!out) { sgs::g_last_error = "out is NULL"; return SEGSALSA_ERR_ARG; }
+  *out = nullptr;
+  std::unique_ptr<sgs::SolverBase> impl;
+  std::string msg;
+  int rc = sgs::create_any(pr, ws, wsb, impl, msg);
+  if (rc) { sgs::g_last_error = msg; return rc; }
+  auto* h = new segsalsa_str;
+  h->impl = std::move(impl);
+  *out = h;
+  return SEGSALSA_OK;
+}
+
+#define SGS_H(h) if (!(h)) return SEGSALSA_ERR_ARG
+
+int segsalsa_str_set_probs(segsalsa_str_t* h, const void* p, int32_t layout, int32_t dev) {
+  SGS_H(h); return h->impl->set_probs(p, layout, dev);
+}
+int segsalsa_str_solve(segsalsa_str_t* h, int32_t iters, double* trace, int32_t every, int32_t* nrec) {
+  SGS_H(h); return h->impl->solve(iters, trace, every, nrec);
+}
+int segsalsa_str_get_labels(segsalsa_str_t* h, int32_t* lab, int32_t dev) {
+  SGS_H(h); return h->impl->get_labels(lab, dev);
+}
+int segsalsa_str_get_z(segsalsa_str_t* h, void* z, int32_t layout, int32_t dev) {
+  SGS_H(h); return h->impl->get_z(z, layout, dev);
+}
+int segsalsa_str_get_iteration(const segsalsa_str_t* h, int32_t* k) {
+  SGS_H(h); return h->impl->get_iteration(k);
+}
+int segsalsa_str_get_state(segsalsa_str_t* h, void* z, void* d1, void* d2, void* d3, void* d4,
+                           void* rhs, int32_t dev) {
+  SGS_H(h); return h->impl->get_state(z, d1, d2, d3, d4, rhs, dev);
+}
+int segsalsa_str_set_state(segsalsa_str_t* h, const void* z, const void* d1, const void* d2,
+                           const void* d3, const void* d4, const void* rhs, int32_t k, int32_t dev) {
+  SGS_H(h); return h->impl->set_state(z, d1, d2, d3, d4, rhs, k, dev);
+}
+int segsalsa_str_linear_solve(segsalsa_str_t* h, const void* rhs, void* z, int32_t dev) {
+  SGS_H(h); return h->impl->linear_solve(rhs, z, dev);
+}
+int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on) {
+  SGS_H(h); return h->impl->set_profiling(on);
+}
+int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms) {
+  SGS_H(h); return h->impl->kernel_stats(launches, ms);
+}
+int segsalsa_str_reset_stats(segsalsa_str_t* h) {
+  SGS_H(h); return h->impl->reset_stats();
+}
+int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sw, double* it) {
+  SGS_H(h); return h->impl->traffic(sw, it);
+}
+void segsalsa_str_destroy(segsalsa_str_t* h) { delete h; }
+const char* segsalsa_str_last_error(const segsalsa_str_t* h) {
+  if (!h) return sgs::g_last_error.c_str();
+  return h->impl->err.c_str();
+}
+
+}  // extern "C"
