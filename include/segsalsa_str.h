@@ -137,6 +137,26 @@ int segsalsa_str_set_state(segsalsa_str_t* h, const void* z, const void* d1, con
  * rhs and z pixel-major (H, W, K). Leaves the solver state untouched. */
 int segsalsa_str_linear_solve(segsalsa_str_t* h, const void* rhs, void* z, int32_t on_device);
 
+/* Allocation-free z-update. The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (code running under a fixed memory budget or an outside
+ * allocator, or a plug-in without a handle). It solves (3 I + c (D_h^T D_h + D_v^T D_v)) z = rhs
+ * with periodic boundaries, which is the z-update operator (3 I + J^T J) of a handle whose shift
+ * weights have sum_j omega_j^2 = c_omega (1 for the default normalised Gaussian weights).
+ *  - rhs, z: FP32 device memory, pixel-major (H, W, K), owned by the caller; z may not alias rhs.
+ *  - Scratch: one file-scope device array (16 MiB spectrum + 512 KiB tables) that every GPU
+ *    loading the library holds until exit. Limits: H*(W/2+1)*K <= 2097152, W <= 8192 when W has
+ *    no prime factor above 7 and W <= 4096 otherwise, H <= 3200, 2 <= H, W, 1 <= K <= 32.
+ *    Sizes beyond them return SEGSALSA_ERR_OOM; other bad arguments SEGSALSA_ERR_ARG.
+ *  - No cudaMalloc / cudaFree or other device allocation happens in any call. The first call on
+ *    a device looks up the array's device address and builds the tables (make it before any
+ *    stream capture); later calls rebuild the tables only when H, W or c_omega change.
+ *  - Runs asynchronously on `stream` (cudaStream_t, NULL = legacy default stream). Every call
+ *    shares the one array, so calls that overlap on the GPU (other streams, other threads)
+ *    race; nothing in it needs to start at zero, because each call writes every spectrum entry
+ *    it reads. Not thread-safe. No message is stored: the status code is the error report. */
+int segsalsa_str_linear_solve_static(const float* rhs, float* z, int32_t H, int32_t W, int32_t K,
+                                     double c_omega, void* stream);
+
 /* Measurement hooks. set_profiling(1) records CUDA events around each kernel launch of
  * solve() so that kernel_stats() can report, per kernel kind, the launch count and the total
  * device time in milliseconds since the last reset. Kernel kinds (index):

@@ -35,7 +35,7 @@ SYMBOLS = (
     "segsalsa_str_get_iteration", "segsalsa_str_get_state", "segsalsa_str_set_state",
     "segsalsa_str_linear_solve", "segsalsa_str_set_profiling", "segsalsa_str_kernel_stats",
     "segsalsa_str_reset_stats", "segsalsa_str_traffic_model", "segsalsa_str_destroy",
-    "segsalsa_str_last_error",
+    "segsalsa_str_last_error", "segsalsa_str_linear_solve_static",
 )
 
 
@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "segsalsa_str_traffic_model": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "segsalsa_str_destroy": (None, [vp]),
         "segsalsa_str_last_error": (C.c_char_p, [vp]),
+        "segsalsa_str_linear_solve_static": (C.c_int, [vp, vp, i32, i32, i32, C.c_double, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -147,6 +148,20 @@ def segsalsa_str_destroy(h):
 
 def segsalsa_str_last_error(h=None) -> str:
     return load().segsalsa_str_last_error(h).decode()
+
+
+def segsalsa_str_linear_solve_static(rhs, z, c_omega: float = 1.0, stream=None) -> int:
+    """Allocation-free z-update for callers that cannot allocate device memory: rhs and z are
+    FP32 device tensors of shape (H, W, K); the scratch is the library's static device array.
+    Returns the status code (0 on success) without raising."""
+    H, W, K = (int(v) for v in rhs.shape)
+    if tuple(z.shape) != (H, W, K):
+        raise ValueError("rhs and z must have the same (H, W, K) shape")
+    p1, d1 = _ptr(rhs, np.float32)
+    p2, d2 = _ptr(z, np.float32)
+    if not (d1 and d2):
+        raise ValueError("rhs and z must be device tensors")
+    return load().segsalsa_str_linear_solve_static(p1, p2, H, W, K, float(c_omega), stream)
 
 
 def make_params(H, W, K, M=1, sigma=0.5, lam=1.5, mu=1.0, schatten_p=1, precision="fp32",
