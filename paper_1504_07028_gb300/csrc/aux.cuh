@@ -72,44 +72,40 @@ __global__ void k_labels(const T* z, int n, int K, int32_t* lab) {
 // Euclidean projection of every pixel vector onto the probability simplex (Michelot's
 // active-set iteration: theta = (sum of the active entries - 1) / |active|, drop entries
 // <= theta, repeat; exact after at most K rounds), plus per-block partials of
-// min z, max |1^T z - 1| and sum_i -ln(p_i^T proj(z_i)).
-template <typename T>
+// min z, max |1^T z - 1| and sum_i -ln(p_i^T proj(z_i)). G lanes per pixel, class k on lane k.
+template <typename T, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p, T* zp, int n,
                                                         int K, double* part /*[blocks][3]*/) {
   __shared__ double red32[32];
+  constexpr int PPB = AUX_THREADS / G;
+  const int g = threadIdx.x % G;
   T vmin = T(1e30), vdev = T(0), vdata = T(0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const T* zi = z + (size_t)i * K;
-    T v[32];
-    unsigned act = 0;
-    T s = T(0);
-    for (int k = 0; k < K; ++k) {
-      v[k] = zi[k];
-      s += v[k];
-      vmin = fmin(vmin, v[k]);
-      act |= 1u << k;
-    }
-    vdev = fmax(vdev, fabs(s - T(1)));
+  pdl_wait();
+  for (int i0 = blockIdx.x * PPB; i0 < n; i0 += gridDim.x * PPB) {
+    const int i = i0 + threadIdx.x / G;
+    const bool ok = i < n && g < K;
+    const T v = ok ? z[(size_t)i * K + g] : T(0);
+    const T pk = ok ? p[(size_t)i * K + g] : T(0);
+    bool act = ok;
+    const T s = group_sum<G>(v);
     T theta = T(0);
     for (int round = 0; round <= K; ++round) {
-      T sa = T(0);
-      int na = 0;
-      for (int k = 0; k < K; ++k)
-        if (act >> k & 1u) { sa += v[k]; ++na; }
-      theta = (sa - T(1)) / T(na);
-      unsigned nact = act;
-      for (int k = 0; k < K; ++k)
-        if ((act >> k & 1u) && v[k] <= theta) nact &= ~(1u << k);
-      if (nact == act || nact == 0) break;
+      const T sa = group_sum<G>(act ? v : T(0));
+      const T na = group_sum<G>(act ? T(1) : T(0));
+      theta = (sa - T(1)) / fmax(na, T(1));
+      const bool nact = act && v > theta;
+      const bool changed = act && !nact;
       act = nact;
+      if (!__any_sync(0xffffffffu, changed)) break;  // warp-uniform exit (groups share shuffles)
     }
-    T pz = T(0);
-    for (int k = 0; k < K; ++k) {
-      const T q = fmax(v[k] - theta, T(0));
-      zp[(size_t)i * K + k] = q;
-      pz += p[(size_t)i * K + k] * q;
+    const T q = ok ? fmax(v - theta, T(0)) : T(0);
+    if (ok) zp[(size_t)i * K + g] = q;
+    const T pz = group_sum<G>(pk * q);
+    if (ok) vmin = fmin(vmin, v);
+    if (i < n && g == 0) {
+      vdev = fmax(vdev, fabs(s - T(1)));
+      vdata -= log(pz);
     }
-    vdata -= log(pz);
   }
   const double a = block_min_d((double)vmin, red32);
   if (threadIdx.x == 0) part[3 * blockIdx.x + 0] = a;
@@ -119,41 +115,104 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
   if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = c;
 }
 
-// sum_i ||[J zp]_i||_{S_p} per block (zp pixel-major), via the 2x2 Gram matrix of eq. (5).
-// Per-pixel arithmetic in T, block sums in double; grid-stride over pixels.
-template <typename T>
+// sum_i ||[J zp]_i||_{S_p} per block (zp pixel-major), via the 2x2 Gram matrix of eq. (5):
+// G lanes per pixel (class k on lane k) accumulate their 2L Jacobian entries, a G-lane sum
+// gives the Gram matrix. Block sums in double.
+template <typename T, int M, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* omega, int H, int W,
-                                                      int K, int M, int sp, double* part) {
+                                                      int K, int sp, double* part) {
   __shared__ double red32[32];
+  constexpr int PPB = AUX_THREADS / G;
+  constexpr int P = 2 * M + 1;
+  const int g = threadIdx.x % G;
+  const int n = H * W;
   T val = T(0);
-  const int P = 2 * M + 1;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * W; i += gridDim.x * blockDim.x) {
-    const int y = i / W, x = i % W;
+  pdl_wait();
+  for (int i0 = blockIdx.x * PPB; i0 < n; i0 += gridDim.x * PPB) {
+    const int i = i0 + threadIdx.x / G;
+    const bool ok = i < n && g < K;
+    const int y = ok ? i / W : 0, x = ok ? i % W : 0;
+    T zv[P + 1][P + 1];
+    int xs[P + 1];
+#pragma unroll
+    for (int dx = 0; dx <= P; ++dx) {
+      int xx = x - M + dx;
+      xx += (xx < 0) ? W : 0;
+      xx -= (xx >= W) ? W : 0;
+      xs[dx] = xx;
+    }
+#pragma unroll
+    for (int dy = 0; dy <= P; ++dy) {
+      int yy = y - M + dy;
+      yy += (yy < 0) ? H : 0;
+      yy -= (yy >= H) ? H : 0;
+      const size_t row = (size_t)yy * W;
+#pragma unroll
+      for (int dx = 0; dx <= P; ++dx)
+        zv[dy][dx] = (ok && !(dy == P && dx == P)) ? zp[(row + xs[dx]) * K + g] : T(0);
+    }
     T a = T(0), b = T(0), c = T(0);
-    for (int dy = -M; dy <= M; ++dy)
-      for (int dx = -M; dx <= M; ++dx) {
-        const T w = omega[(dy + M) * P + (dx + M)];
-        const int y0 = wrap_idx(y + dy, H), x0 = wrap_idx(x + dx, W);
-        const int y1 = wrap_idx(y0 + 1, H), x1 = wrap_idx(x0 + 1, W);
-        const T* z00 = zp + ((size_t)y0 * W + x0) * K;
-        const T* z01 = zp + ((size_t)y0 * W + x1) * K;
-        const T* z10 = zp + ((size_t)y1 * W + x0) * K;
-        for (int k = 0; k < K; ++k) {
-          const T h = w * (z01[k] - z00[k]);
-          const T v = w * (z10[k] - z00[k]);
-          a += h * h;
-          b += h * v;
-          c += v * v;
-        }
+#pragma unroll
+    for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < P; ++dx) {
+        const T w = omega[dy * P + dx];
+        const T h = w * (zv[dy][dx + 1] - zv[dy][dx]);
+        const T v = w * (zv[dy + 1][dx] - zv[dy][dx]);
+        a += h * h;
+        b += h * v;
+        c += v * v;
       }
-    const T hd = T(0.5) * (a - c);
-    const T r = sqrt(hd * hd + b * b);
-    const T s1 = sqrt(fmax(T(0.5) * (a + c) + r, T(0)));
-    const T s2 = sqrt(fmax(T(0.5) * (a + c) - r, T(0)));
-    val += (sp == 1) ? s1 + s2 : (sp == 2) ? sqrt(fmax(a + c, T(0))) : s1;
+    a = group_sum<G>(a);
+    b = group_sum<G>(b);
+    c = group_sum<G>(c);
+    if (i < n && g == 0) {
+      const T hd = T(0.5) * (a - c);
+      const T r = sqrt(hd * hd + b * b);
+      const T s1 = sqrt(fmax(T(0.5) * (a + c) + r, T(0)));
+      const T s2 = sqrt(fmax(T(0.5) * (a + c) - r, T(0)));
+      val += (sp == 1) ? s1 + s2 : (sp == 2) ? sqrt(fmax(a + c, T(0))) : s1;
+    }
   }
   const double t = block_sum_d((double)val, red32);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+template <typename T, int G>
+inline void launch_project(int blocks, cudaStream_t st, const T* z, const T* p, T* zp, int n,
+                           int K, double* part) {
+  launch_pdl(k_project<T, G>, dim3(blocks), dim3(AUX_THREADS), 0, st, z, p, zp, n, K, part);
+}
+template <typename T>
+inline cudaError_t launch_project_g(int G, int blocks, cudaStream_t st, const T* z, const T* p,
+                                    T* zp, int n, int K, double* part) {
+  switch (G) {
+    case 4: launch_project<T, 4>(blocks, st, z, p, zp, n, K, part); break;
+    case 8: launch_project<T, 8>(blocks, st, z, p, zp, n, K, part); break;
+    case 16: launch_project<T, 16>(blocks, st, z, p, zp, n, K, part); break;
+    default: launch_project<T, 32>(blocks, st, z, p, zp, n, K, part); break;
+  }
+  return cudaGetLastError();
+}
+template <typename T, int M>
+inline void launch_prior_m(int G, int blocks, cudaStream_t st, const T* zp, const T* om, int H,
+                           int W, int K, int sp, double* part) {
+  switch (G) {
+    case 4: launch_pdl(k_prior<T, M, 4>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
+    case 8: launch_pdl(k_prior<T, M, 8>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
+    case 16: launch_pdl(k_prior<T, M, 16>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
+    default: launch_pdl(k_prior<T, M, 32>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
+  }
+}
+template <typename T>
+inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const T* zp,
+                                const T* om, int H, int W, int K, int sp, double* part) {
+  switch (M) {
+    case 0: launch_prior_m<T, 0>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    case 1: launch_prior_m<T, 1>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    default: launch_prior_m<T, 2>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+  }
+  return cudaGetLastError();
 }
 
 // Sum of squares of G^T d, gathered from the tile partials P2 like the row pass does.
@@ -165,6 +224,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_gather_sq(const T* P2, const in
   __shared__ double red32[32];
   T val = T(0);
   const size_t tot = (size_t)H * W * K;
+  pdl_wait();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
        i += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(i % K);
@@ -193,15 +253,33 @@ __global__ void k_finalize_trace(const double* sq, int nsq, const double* gsq, i
                                  const double* proj, int nproj, const double* prior, int nprior,
                                  double k, double mu, double lambda, double* rec) {
   __shared__ double red32[32];
+  constexpr int U = 8;  // independent loads in flight per thread
   double a = 0.0, b = 0.0, c = 0.0, d = 0.0, mn = 1e300, mx = 0.0;
-  for (int i = threadIdx.x; i < nsq; i += blockDim.x) a += sq[i];
-  for (int i = threadIdx.x; i < ngsq; i += blockDim.x) b += gsq[i];
+  auto sum = [&](const double* v, int n, int stride, int off) {
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < n) acc[u] += v[stride * i + off];
+      }
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) t += acc[u];
+    return t;
+  };
+  pdl_wait();
+  a = sum(sq, nsq, 1, 0);
+  b = sum(gsq, ngsq, 1, 0);
+  c = sum(proj, nproj, 3, 2);
+  d = sum(prior, nprior, 1, 0);
   for (int i = threadIdx.x; i < nproj; i += blockDim.x) {
     mn = fmin(mn, proj[3 * i]);
     mx = fmax(mx, proj[3 * i + 1]);
-    c += proj[3 * i + 2];
   }
-  for (int i = threadIdx.x; i < nprior; i += blockDim.x) d += prior[i];
   a = block_sum_d(a, red32);
   if (threadIdx.x == 0) rec[1] = sqrt(a);
   b = block_sum_d(b, red32);

@@ -24,7 +24,7 @@
 namespace sgs {
 
 constexpr int FFT_MAXST = 24;
-constexpr int FFT_MAXE = 16;  // complex values held per thread per stage
+constexpr int FFT_MAXE = 16;  // most complex values a thread holds per stage (largest variant)
 
 template <typename T>
 struct FftPlan {
@@ -33,7 +33,9 @@ struct FftPlan {
   int blue;     // 1 when Bluestein is used
   int nst;      // number of Stockham stages
   int radix[FFT_MAXST];
-  int ns[FFT_MAXST];     // product of the radices before this stage
+  int ns[FFT_MAXST];         // product of the radices before this stage
+  uint32_t mg_ns[FFT_MAXST];   // ceil(2^32 / ns) (exact division of indices < 2^16)
+  uint32_t mg_nsr[FFT_MAXST];  // ceil(2^32 / (ns * radix))
   const cplx<T>* tw;     // [Mf] exp(-2 pi i m / Mf)
   const cplx<T>* chirp;  // [N]  exp(i pi m^2 / N)          (Bluestein)
   const cplx<T>* bhat;   // [Mf] DFT of the chirp filter / Mf (Bluestein)
@@ -120,16 +122,23 @@ template <typename C> struct Dft<3, C> : DftOdd<3, C> {};
 template <typename C> struct Dft<5, C> : DftOdd<5, C> {};
 template <typename C> struct Dft<7, C> : DftOdd<7, C> {};
 
-// One forward Stockham stage on B interleaved sequences X[n * B + b] (in place: every thread
-// reads its inputs, the block synchronises, then writes).
-template <typename T, int R>
-__device__ __forceinline__ void fft_stage(cplx<T>* X, int B, int Mf, int Ns,
-                                          const cplx<T>* __restrict__ tw) {
+// floor(t / d) for t < 2^16 with mg = ceil(2^32 / d) (mg = 0 encodes d = 1).
+__device__ __forceinline__ int qdiv(int t, uint32_t mg) {
+  return mg ? (int)__umulhi((uint32_t)t, mg) : t;
+}
+
+// One forward Stockham stage of radix R in {2,3,4,5,7,8} on B = 2^lgB interleaved sequences
+// X[n * B + b]: each work item is one radix-R butterfly (in place: every thread reads its
+// inputs, the block synchronises, then writes).
+template <typename T, int R, int MAXE>
+__device__ __forceinline__ void fft_stage(cplx<T>* X, int lgB, int Mf, int Ns, uint32_t mg,
+                                          const cplx<T>* tw) {
   using C = cplx<T>;
-  constexpr int MI = (FFT_MAXE + R - 1) / R;
+  constexpr int MI = (MAXE + R - 1) / R;
+  const int B = 1 << lgB;
   const int nb = Mf / R;
-  const int items = nb * B;
-  const int stride = Mf / (Ns * R);
+  const int items = nb << lgB;
+  const int stride = nb / Ns;
   C out[MI][R];
   int base[MI];
 #pragma unroll
@@ -137,17 +146,18 @@ __device__ __forceinline__ void fft_stage(cplx<T>* X, int B, int Mf, int Ns,
     const int it = threadIdx.x + q * blockDim.x;
     base[q] = -1;
     if (it < items) {
-      const int b = it % B, t = it / B;
-      const int j = t % Ns;
+      const int b = it & (B - 1), t = it >> lgB;
+      const int g = qdiv(t, mg);
+      const int j = t - g * Ns;
       C v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = X[(t + r * nb) * B + b];
+      for (int r = 0; r < R; ++r) v[r] = X[((t + r * nb) << lgB) + b];
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * j * stride]);
       Dft<R, C>::run(v);
 #pragma unroll
       for (int r = 0; r < R; ++r) out[q][r] = v[r];
-      base[q] = ((t / Ns) * Ns * R + j) * B + b;
+      base[q] = ((g * Ns * R + j) << lgB) + b;
     }
   }
   __syncthreads();
@@ -155,64 +165,152 @@ __device__ __forceinline__ void fft_stage(cplx<T>* X, int B, int Mf, int Ns,
   for (int q = 0; q < MI; ++q) {
     if (base[q] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) X[base[q] + r * Ns * B] = out[q][r];
+      for (int r = 0; r < R; ++r) X[base[q] + ((r * Ns) << lgB)] = out[q][r];
     }
   }
   __syncthreads();
 }
 
-template <typename T>
-__device__ void fft_forward(cplx<T>* X, int B, const FftPlan<T>& pl) {
-  for (int s = 0; s < pl.nst; ++s) {
-    const int Ns = pl.ns[s];
-    switch (pl.radix[s]) {
-      case 8: fft_stage<T, 8>(X, B, pl.Mf, Ns, pl.tw); break;
-      case 4: fft_stage<T, 4>(X, B, pl.Mf, Ns, pl.tw); break;
-      case 2: fft_stage<T, 2>(X, B, pl.Mf, Ns, pl.tw); break;
-      case 3: fft_stage<T, 3>(X, B, pl.Mf, Ns, pl.tw); break;
-      case 5: fft_stage<T, 5>(X, B, pl.Mf, Ns, pl.tw); break;
-      case 7: fft_stage<T, 7>(X, B, pl.Mf, Ns, pl.tw); break;
+// A Stockham stage of prime radix R > 7 computed output by output: output o of sequence b is
+// sum_r X[t + r nb] w^{r (j s + m nb)} with o = g Ns R + m Ns + j, t = g Ns + j, s = nb / Ns
+// (twiddle and the radix-R DFT root folded into one table index). MAXE outputs per thread.
+template <typename T, int MAXE>
+__device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int lgB, int Mf, int R, int Ns,
+                                                 uint32_t mg_ns, uint32_t mg_nsr,
+                                                 const cplx<T>* tw) {
+  using C = cplx<T>;
+  const int B = 1 << lgB;
+  const int nb = Mf / R;
+  const int items = Mf << lgB;
+  const int s = nb / Ns;
+  const int NsR = Ns * R;
+  C out[MAXE];
+#pragma unroll
+  for (int q = 0; q < MAXE; ++q) {
+    const int it = threadIdx.x + q * blockDim.x;
+    out[q] = mkc<T>(T(0), T(0));
+    if (it < items) {
+      const int b = it & (B - 1), o = it >> lgB;
+      const int g = qdiv(o, mg_nsr);
+      const int rem = o - g * NsR;
+      const int m = qdiv(rem, mg_ns);
+      const int j = rem - m * Ns;
+      const int t = g * Ns + j;
+      int step = j * s + m * nb;
+      step -= (step >= Mf) ? Mf : 0;
+      int idx = 0;
+      T ax = T(0), ay = T(0);
+      const C* src = X + (t << lgB) + b;
+      for (int r = 0; r < R; ++r) {
+        const C v = src[(r * nb) << lgB];
+        const C w = tw[idx];
+        ax += v.x * w.x - v.y * w.y;
+        ay += v.x * w.y + v.y * w.x;
+        idx += step;
+        idx -= (idx >= Mf) ? Mf : 0;
+      }
+      out[q].x = ax;
+      out[q].y = ay;
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MAXE; ++q) {
+    const int it = threadIdx.x + q * blockDim.x;
+    if (it < items) X[it] = out[q];
+  }
+  __syncthreads();
+}
+
+// Shared-memory copies of the transform tables, filled at kernel start.
+template <typename T>
+struct FftTables {
+  const cplx<T>* tw;
+  const cplx<T>* chirp;
+  const cplx<T>* bhat;
+};
+
+template <typename T, int MAXE>
+__device__ void fft_forward(cplx<T>* X, int lgB, const FftPlan<T>& pl, const cplx<T>* tw) {
+  for (int s = 0; s < pl.nst; ++s) {
+    const int Ns = pl.ns[s];
+    const uint32_t mg = pl.mg_ns[s];
+    switch (pl.radix[s]) {
+      case 8: fft_stage<T, 8, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 4: fft_stage<T, 4, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 2: fft_stage<T, 2, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 3: fft_stage<T, 3, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 5: fft_stage<T, 5, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 7: fft_stage<T, 7, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      default:
+        fft_direct_stage<T, MAXE>(X, lgB, pl.Mf, pl.radix[s], Ns, mg, pl.mg_nsr[s], tw);
+        break;
+    }
+  }
+}
+
+// Bytes of shared memory for the tables of a plan (twiddles, and for Bluestein the chirp and
+// the filter spectrum).
+template <typename T>
+__host__ __device__ inline size_t fft_table_bytes(int N, int Mf, int blue) {
+  return sizeof(cplx<T>) * ((size_t)Mf + (blue ? (size_t)N + Mf : 0));
+}
+
+// Start the asynchronous copies of the tables into `tab` (caller commits and waits).
+template <typename T>
+__device__ inline FftTables<T> load_tables(const FftPlan<T>& pl, cplx<T>* tab) {
+  constexpr int CB = sizeof(cplx<T>);
+  for (int i = threadIdx.x; i < pl.Mf; i += blockDim.x) cp_async_zfill<CB>(tab + i, pl.tw + i, true);
+  FftTables<T> t{tab, nullptr, nullptr};
+  if (pl.blue) {
+    cplx<T>* ch = tab + pl.Mf;
+    cplx<T>* bh = ch + pl.N;
+    for (int i = threadIdx.x; i < pl.N; i += blockDim.x) cp_async_zfill<CB>(ch + i, pl.chirp + i, true);
+    for (int i = threadIdx.x; i < pl.Mf; i += blockDim.x) cp_async_zfill<CB>(bh + i, pl.bhat + i, true);
+    t.chirp = ch;
+    t.bhat = bh;
+  }
+  return t;
 }
 
 // Forward DFT of length N of the B sequences in X (slots [0, N) filled, Bluestein slots
 // [N, Mf) need not be). Afterwards X[k*B + b], k < N, holds X_k for the mixed-radix path; for
 // Bluestein the caller reads bluestein_out(k).
-template <typename T>
-__device__ void dft_rows(cplx<T>* X, int B, const FftPlan<T>& pl) {
-  using C = cplx<T>;
+template <typename T, int MAXE>
+__device__ void dft_rows(cplx<T>* X, int lgB, const FftPlan<T>& pl, const FftTables<T>& tb) {
   if (!pl.blue) {
-    fft_forward<T>(X, B, pl);
+    fft_forward<T, MAXE>(X, lgB, pl, tb.tw);
     return;
   }
   // a_n = x_n conj(chirp_n), zero padded
-  for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x) {
-    const int n = i / B;
-    X[i] = (n < pl.N) ? cmulc(X[i], pl.chirp[n]) : mkc<T>(T(0), T(0));
+  for (int i = threadIdx.x; i < (pl.Mf << lgB); i += blockDim.x) {
+    const int n = i >> lgB;
+    X[i] = (n < pl.N) ? cmulc(X[i], tb.chirp[n]) : mkc<T>(T(0), T(0));
   }
   __syncthreads();
-  fft_forward<T>(X, B, pl);
-  for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x)
-    X[i] = cconj(cmul(X[i], pl.bhat[i / B]));
+  fft_forward<T, MAXE>(X, lgB, pl, tb.tw);
+  for (int i = threadIdx.x; i < (pl.Mf << lgB); i += blockDim.x)
+    X[i] = cconj(cmul(X[i], tb.bhat[i >> lgB]));
   __syncthreads();
-  fft_forward<T>(X, B, pl);  // = conj(cyclic convolution)
+  fft_forward<T, MAXE>(X, lgB, pl, tb.tw);  // = conj(cyclic convolution)
 }
 
 // Value X_k after dft_rows.
 template <typename T>
-__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* X, int B, int k, int b,
-                                           const FftPlan<T>& pl) {
-  const cplx<T> v = X[k * B + b];
+__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* X, int lgB, int k, int b,
+                                           const FftPlan<T>& pl, const FftTables<T>& tb) {
+  const cplx<T> v = X[(k << lgB) + b];
   if (!pl.blue) return v;
-  return cconj(cmul(pl.chirp[k], v));  // conj(chirp_k) * (a * b)_k
+  return cconj(cmul(tb.chirp[k], v));  // conj(chirp_k) * (a * b)_k
 }
 
 // ------------------------------------------------------------------- pass A (forward rows)
 template <typename T>
 struct RowArgs {
   int H, W, K, Wh;       // Wh = W/2 + 1 stored frequencies
-  int QB;                // class pairs per CTA
+  int QB;                // class pairs per CTA (a power of two)
+  int lgB;               // log2(QB)
+  int smem_tables;       // 1: copy the transform tables to shared memory
   FftPlan<T> pl;
   // source of rhs: dense [n][K] (src != null) or the sweep partials
   const T* src;
@@ -220,10 +318,13 @@ struct RowArgs {
   int ntx, EHmax, EWmax;
   const int* covY;       // [H][2]: (tile row << 16 | ext row), -1 when absent
   const int* covX;       // [W][2]: (tile col << 16 | ext col)
+  const int* offX;       // [W][2]: (tile col * EHmax * EWmax + ext col) * K, -1 when absent
   cplx<T>* S;            // [H][Wh][K]
   T* z;                  // pass C output [n][K]
 };
 
+// rhs(y, x, k) as the fixed-order sum of the (at most 2 x 2) tile partials covering (y, x);
+// covY / covX entries are (tile << 16 | position in the tile + halo), -1 when absent.
 template <typename T>
 __device__ __forceinline__ T gather_rhs(const RowArgs<T>& a, int y, int x, int k) {
   if (a.src) return a.src[((size_t)y * a.W + x) * a.K + k];
@@ -245,35 +346,100 @@ __device__ __forceinline__ T gather_rhs(const RowArgs<T>& a, int y, int x, int k
   return v;
 }
 
+// Same sum for a row whose two vertical covers start at P offsets rb0 / rb1 (-1 when absent),
+// with the per-column offsets offX in shared memory. Same summation order as gather_rhs.
 template <typename T>
-__global__ void __launch_bounds__(512) k_row_forward(const RowArgs<T> a) {
+__device__ __forceinline__ T gather_row(const T* P, int rb0, int rb1, const int* oX, int x, int k) {
+  T v = T(0);
+  const int o0 = oX[2 * x], o1 = oX[2 * x + 1];
+  if (rb0 >= 0) {
+    if (o0 >= 0) v += P[rb0 + o0 + k];
+    if (o1 >= 0) v += P[rb0 + o1 + k];
+  }
+  if (rb1 >= 0) {
+    if (o0 >= 0) v += P[rb1 + o0 + k];
+    if (o1 >= 0) v += P[rb1 + o1 + k];
+  }
+  return v;
+}
+
+// P offset of the row start of vertical cover cy = (tile row << 16 | ext row), -1 if absent.
+template <typename T>
+__device__ __forceinline__ int cover_row_base(const RowArgs<T>& a, int cy) {
+  if (cy < 0) return -1;
+  return (((cy >> 16) * a.ntx * a.EHmax) + (cy & 0xffff)) * a.EWmax * a.K;
+}
+
+// Shared memory of a row-pass CTA: transform buffer, tables, horizontal offset table.
+template <typename T>
+__host__ __device__ inline size_t row_smem_bytes(int N, int Mf, int blue, int QB, int tables) {
+  return sizeof(cplx<T>) * (size_t)Mf * QB + (tables ? fft_table_bytes<T>(N, Mf, blue) : 0) +
+         sizeof(int) * 2 * (size_t)N;
+}
+template <typename T>
+__device__ inline FftTables<T> row_tables(const RowArgs<T>& a, cplx<T>* tab) {
+  if (a.smem_tables) return load_tables<T>(a.pl, tab);
+  return FftTables<T>{a.pl.tw, a.pl.chirp, a.pl.bhat};
+}
+
+template <typename T, int MAXE>
+__global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int U = 4;  // independent element loads in flight per thread
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
   const int y = blockIdx.x;
   const int q0 = blockIdx.y * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
+  C* tab = X + (size_t)a.pl.Mf * B;
+  int* cX = reinterpret_cast<int*>(
+      tab + (a.smem_tables ? fft_table_bytes<T>(N, a.pl.Mf, a.pl.blue) / sizeof(C) : 0));
+  const FftTables<T> tb = row_tables<T>(a, tab);
+  if (!a.src)
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) cp_async_zfill<4>(cX + i, a.offX + i, true);
+  cp_async_commit();
+  pdl_wait();  // rhs / partials come from the previous kernel
+  cp_async_wait_all();
+  __syncthreads();
   T* Xf = reinterpret_cast<T*>(X);
   // load: two classes per complex sequence (real part class 2q, imaginary part class 2q+1)
-  for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
-    const int part = i & 1;
-    const int qq = (i >> 1) % B;
-    const int x = (i >> 1) / B;
-    const int k = 2 * (q0 + qq) + part;
-    Xf[i] = (k < a.K) ? gather_rhs(a, y, x, k) : T(0);
+  const int tot = N * B * 2;
+  const int rb0 = a.src ? -1 : cover_row_base(a, a.covY[2 * y]);
+  const int rb1 = a.src ? -1 : cover_row_base(a, a.covY[2 * y + 1]);
+  for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = T(0);
+      if (i < tot) {
+        const int part = i & 1;
+        const int qq = (i >> 1) & (B - 1);
+        const int x = (i >> 1) >> a.lgB;
+        const int k = 2 * (q0 + qq) + part;
+        if (k < a.K)
+          v[u] = a.src ? a.src[((size_t)y * a.W + x) * a.K + k] : gather_row<T>(a.P, rb0, rb1, cX, x, k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < tot) Xf[i] = v[u];
+    }
   }
   __syncthreads();
-  dft_rows<T>(X, B, a.pl);
+  dft_rows<T, MAXE>(X, a.lgB, a.pl, tb);
+  pdl_trigger();
   // unpack the two real spectra: A = (X_k + conj X_{N-k})/2, B = (X_k - conj X_{N-k})/(2i)
   for (int i = threadIdx.x; i < a.Wh * B * 2; i += blockDim.x) {
     const int part = i & 1;
-    const int qq = (i >> 1) % B;
-    const int kx = (i >> 1) / B;
+    const int qq = (i >> 1) & (B - 1);
+    const int kx = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C u = dft_out<T>(X, B, kx, qq, a.pl);
-    const C w = dft_out<T>(X, B, (kx == 0) ? 0 : N - kx, qq, a.pl);
+    const C u = dft_out<T>(X, a.lgB, kx, qq, a.pl, tb);
+    const C w = dft_out<T>(X, a.lgB, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
     C o;
     if (part == 0) { o.x = T(0.5) * (u.x + w.x); o.y = T(0.5) * (u.y - w.y); }
     else           { o.x = T(0.5) * (u.y + w.y); o.y = T(0.5) * (w.x - u.x); }
@@ -292,41 +458,63 @@ __global__ void k_gather_dense(const RowArgs<T> a) {
 }
 
 // ------------------------------------------------------------------- pass C (inverse rows)
-template <typename T>
-__global__ void __launch_bounds__(512) k_row_inverse(const RowArgs<T> a) {
+template <typename T, int MAXE>
+__global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int U = 4;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
   const int y = blockIdx.x;
   const int q0 = blockIdx.y * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
+  C* tab = X + (size_t)a.pl.Mf * B;
+  const FftTables<T> tb = row_tables<T>(a, tab);
+  cp_async_commit();
+  pdl_wait();  // the spectrum comes from the column pass
   // load conj(A + iB) over the full frequency range (Hermitian extension), inverse DFT by
   // conj(DFT(conj(.)))/N
-  for (int i = threadIdx.x; i < N * B; i += blockDim.x) {
-    const int qq = i % B;
-    const int kx = i / B;
-    const int ka = 2 * (q0 + qq), kb = ka + 1;
-    const bool lo = kx < a.Wh;
-    const int ks = lo ? kx : N - kx;
-    const C* row = a.S + ((size_t)y * a.Wh + ks) * a.K;
-    C A = (ka < a.K) ? row[ka] : mkc<T>(T(0), T(0));
-    C Bv = (kb < a.K) ? row[kb] : mkc<T>(T(0), T(0));
-    if (!lo) { A = cconj(A); Bv = cconj(Bv); }
-    // X = A + i B; store conj(X)
-    C xv; xv.x = A.x - Bv.y; xv.y = -(A.y + Bv.x);
-    X[i] = xv;
+  const int tot = N * B;
+  for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
+    C Av[U], Bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      Av[u] = mkc<T>(T(0), T(0));
+      Bv[u] = Av[u];
+      if (i < tot) {
+        const int qq = i & (B - 1);
+        const int kx = i >> a.lgB;
+        const int ka = 2 * (q0 + qq), kb = ka + 1;
+        const int ks = kx < a.Wh ? kx : N - kx;
+        const C* row = a.S + ((size_t)y * a.Wh + ks) * a.K;
+        if (ka < a.K) Av[u] = row[ka];
+        if (kb < a.K) Bv[u] = row[kb];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < tot) {
+        C A = Av[u], Bq = Bv[u];
+        if ((i >> a.lgB) >= a.Wh) { A = cconj(A); Bq = cconj(Bq); }
+        C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);   // conj(A + i B)
+        X[i] = xv;
+      }
+    }
   }
+  cp_async_wait_all();
   __syncthreads();
-  dft_rows<T>(X, B, a.pl);
+  dft_rows<T, MAXE>(X, a.lgB, a.pl, tb);
+  pdl_trigger();
   const T inv = T(1) / T(N);
   for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
     const int part = i & 1;
-    const int qq = (i >> 1) % B;
-    const int x = (i >> 1) / B;
+    const int qq = (i >> 1) & (B - 1);
+    const int x = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C v = dft_out<T>(X, B, x, qq, a.pl);     // DFT(conj X)_x ; result = conj(v)/N
+    const C v = dft_out<T>(X, a.lgB, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
     a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
   }
 }
@@ -347,17 +535,21 @@ struct ColArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);  // [H][2*CB]
   const int c0 = blockIdx.x * a.CB;
   const int nseq = 2 * a.CB;
   const int H = a.H;
   T* Sf = reinterpret_cast<T*>(a.S);
+  pdl_wait();  // the spectrum comes from the row pass
   for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
     const int y = i / nseq, s = i % nseq;
     const int col2 = 2 * c0 + s;
-    buf[i] = (col2 < 2 * a.C) ? Sf[(size_t)y * 2 * a.C + col2] : T(0);
+    const bool v = col2 < 2 * a.C;
+    cp_async_zfill<sizeof(T)>(buf + i, v ? Sf + (size_t)y * 2 * a.C + col2 : Sf, v);
   }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   const int s = threadIdx.x % nseq, seg = threadIdx.x / nseq;
   const bool act = seg < a.NSEG;
@@ -370,7 +562,12 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   // causal start value y_{s0-1} = sum_m beta^m r_{s0-1-m}
   T acc = T(0);
   if (act) {
-    for (int m = nw; m >= 1; --m) acc = beta * acc + buf[wrap_idx(s0 - m, H) * nseq + s];
+    int n = s0 - nw;
+    n += (n < 0) ? H : 0;
+    for (int m = nw; m >= 1; --m) {
+      acc = beta * acc + buf[n * nseq + s];
+      n = (n + 1 == H) ? 0 : n + 1;
+    }
     acc *= wf;
   }
   __syncthreads();
@@ -383,7 +580,12 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   // anti-causal start value q_{s1} = sum_m beta^m y_{s1+m}
   T acc2 = T(0);
   if (act) {
-    for (int m = nw; m >= 1; --m) acc2 = beta * acc2 + buf[wrap_idx(s1 - 1 + m, H) * nseq + s];
+    int n = s1 - 1 + nw;
+    n -= (n >= H) ? H : 0;
+    for (int m = nw; m >= 1; --m) {
+      acc2 = beta * acc2 + buf[n * nseq + s];
+      n = (n == 0) ? H - 1 : n - 1;
+    }
     acc2 *= wf;
   }
   __syncthreads();
@@ -392,6 +594,7 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
       acc2 = beta * acc2 + buf[n * nseq + s];
       buf[n * nseq + s] = gain * acc2;
     }
+  pdl_trigger();
   __syncthreads();
   for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
     const int y = i / nseq, ss = i % nseq;
@@ -399,5 +602,187 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
     if (col2 < 2 * a.C) Sf[(size_t)y * 2 * a.C + col2] = buf[i];
   }
 }
+
+// ---------------------------------------------------------------- host-side launch helpers
+struct RowLaunch {
+  int maxe;       // complex values per thread per stage (4, 8 or 16)
+  int threads;
+  int tables;     // tables in shared memory
+  size_t smem;
+};
+
+// Class pairs per CTA for a row transform of length Mf: a power of two, at most 8192 complex
+// values a CTA; halved (down to 128 values a CTA) while the grid has fewer than eight CTAs per
+// SM, so that small images spread over the GPU instead of running long per-CTA chains.
+inline int row_pairs_per_cta(int Mf, int Q, int rows = 1 << 30) {
+  int qb = 1;
+  while (qb < Q && 2 * qb * Mf <= 8192) qb *= 2;
+  while (qb > 1 && (long long)rows * ((Q + qb - 1) / qb) < 8 * 152 && Mf * qb / 2 >= 128) qb /= 2;
+  return qb;
+}
+
+inline uint32_t div_magic(int d) {
+  return d <= 1 ? 0u : (uint32_t)(((1ULL << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+
+// Largest prime factor handled by a direct Stockham stage; rows with a larger prime factor use
+// Bluestein's transform.
+constexpr int FFT_DIRECT_MAX = 127;
+
+inline bool fft_smooth7(long n) {
+  for (long r : {2L, 3L, 5L, 7L})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
+// Transform length and Stockham stages of a row of length N (radices 8, 4, 2, 3, 5, 7 first,
+// then direct prime stages); false when a stage table would overflow.
+inline long largest_prime_factor(long n) {
+  long best = 1;
+  for (long p = 2; p * p <= n; ++p)
+    while (n % p == 0) { best = p; n /= p; }
+  return n > 1 ? (n > best ? n : best) : best;
+}
+
+template <typename T>
+inline bool make_fft_plan(int N, FftPlan<T>& pl) {
+  pl.N = N;
+  if (largest_prime_factor(N) <= FFT_DIRECT_MAX) {
+    pl.Mf = N;
+    pl.blue = 0;
+  } else {
+    long mm = 2L * N - 1;
+    while (!fft_smooth7(mm)) ++mm;
+    pl.Mf = (int)mm;
+    pl.blue = 1;
+  }
+  int rest = pl.Mf, s = 0, ns = 1;
+  auto push = [&](int r) {
+    if (s >= FFT_MAXST) return;
+    pl.radix[s] = r; pl.ns[s] = ns; pl.mg_ns[s] = div_magic(ns); pl.mg_nsr[s] = div_magic(ns * r);
+    ns *= r; ++s; rest /= r;
+  };
+  while (rest % 8 == 0) push(8);
+  while (rest % 4 == 0) push(4);
+  while (rest % 2 == 0) push(2);
+  for (int p : {3, 5, 7})
+    while (rest % p == 0) push(p);
+  for (int p = 11; rest > 1 && p <= FFT_DIRECT_MAX; p += 2)
+    while (rest % p == 0) push(p);
+  pl.nst = s;
+  return rest == 1 && s <= FFT_MAXST;
+}
+
+template <typename T>
+inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB) {
+  RowLaunch r{};
+  const int elems = Mf * QB;
+  r.maxe = 1;
+  while (r.maxe < 16 && (elems + r.maxe - 1) / r.maxe > 1024) r.maxe *= 2;
+  int t = (elems + r.maxe - 1) / r.maxe;
+  t = (t + 31) / 32 * 32;
+  r.threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);
+  r.tables = row_smem_bytes<T>(N, Mf, blue, QB, 1) <= 160 * 1024;
+  r.smem = row_smem_bytes<T>(N, Mf, blue, QB, r.tables);
+  return r;
+}
+
+template <typename K>
+inline cudaError_t grant_smem(K kern, size_t smem, size_t& granted) {
+  if (smem <= granted) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) granted = smem;
+  return e;
+}
+
+// Launchers of the row and column passes: defined (and instantiated for float and double) in
+// fft_f32.cu / fft_f64.cu so that the many kernel variants compile in parallel.
+template <typename T>
+cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLaunch& rl,
+                       cudaStream_t st);
+template <typename T>
+cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem, cudaStream_t st);
+// Grant the dynamic shared memory of the row / column kernels of a plan before any launch.
+template <typename T>
+cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem);
+
+#ifdef SGS_FFT_INSTANTIATE
+template <typename T, int MAXE>
+struct RowGrant {
+  static size_t f, i;
+};
+template <typename T, int MAXE> size_t RowGrant<T, MAXE>::f = 0;
+template <typename T, int MAXE> size_t RowGrant<T, MAXE>::i = 0;
+template <typename T>
+struct ColGrant {
+  static size_t g;
+};
+template <typename T> size_t ColGrant<T>::g = 0;
+
+template <typename T, int MAXE>
+inline cudaError_t prepare_row_inst(size_t smem) {
+  cudaError_t e = grant_smem(k_row_forward<T, MAXE>, smem, RowGrant<T, MAXE>::f);
+  if (e != cudaSuccess) return e;
+  return grant_smem(k_row_inverse<T, MAXE>, smem, RowGrant<T, MAXE>::i);
+}
+
+template <typename T>
+cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem) {
+  cudaError_t e;
+  switch (rl.maxe) {
+    case 1: e = prepare_row_inst<T, 1>(rl.smem); break;
+    case 2: e = prepare_row_inst<T, 2>(rl.smem); break;
+    case 4: e = prepare_row_inst<T, 4>(rl.smem); break;
+    case 8: e = prepare_row_inst<T, 8>(rl.smem); break;
+    default: e = prepare_row_inst<T, 16>(rl.smem); break;
+  }
+  if (e != cudaSuccess) return e;
+  return grant_smem(k_col_solve<T>, col_smem, ColGrant<T>::g);
+}
+
+template <typename T, int MAXE>
+inline cudaError_t launch_row_inst(bool forward, const RowArgs<T>& a, dim3 grid,
+                                   const RowLaunch& rl, cudaStream_t st) {
+  size_t& gf = RowGrant<T, MAXE>::f;
+  size_t& gi = RowGrant<T, MAXE>::i;
+  cudaError_t e;
+  if (forward) {
+    if ((e = grant_smem(k_row_forward<T, MAXE>, rl.smem, gf)) != cudaSuccess) return e;
+    e = launch_pdl(k_row_forward<T, MAXE>, grid, dim3(rl.threads), rl.smem, st, a);
+  } else {
+    if ((e = grant_smem(k_row_inverse<T, MAXE>, rl.smem, gi)) != cudaSuccess) return e;
+    e = launch_pdl(k_row_inverse<T, MAXE>, grid, dim3(rl.threads), rl.smem, st, a);
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLaunch& rl,
+                              cudaStream_t st) {
+  switch (rl.maxe) {
+    case 1: return launch_row_inst<T, 1>(forward, a, grid, rl, st);
+    case 2: return launch_row_inst<T, 2>(forward, a, grid, rl, st);
+    case 4: return launch_row_inst<T, 4>(forward, a, grid, rl, st);
+    case 8: return launch_row_inst<T, 8>(forward, a, grid, rl, st);
+    default: return launch_row_inst<T, 16>(forward, a, grid, rl, st);
+  }
+}
+
+template <typename T>
+cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem,
+                              cudaStream_t st) {
+  cudaError_t e = grant_smem(k_col_solve<T>, smem, ColGrant<T>::g);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_col_solve<T>, dim3(blocks), dim3(threads), smem, st, a);
+}
+
+#else
+extern template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
+extern template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t);
+extern template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
+extern template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
+extern template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
+extern template cudaError_t prepare_fft<double>(const RowLaunch&, size_t);
+#endif
 
 }  // namespace sgs

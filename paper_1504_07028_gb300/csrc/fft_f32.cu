@@ -1,0 +1,9 @@
+// FP32 instantiations of the row-transform and column-solve passes.
+#define SGS_FFT_INSTANTIATE
+#include "fft.cuh"
+
+namespace sgs {
+template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
+template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
+template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
+}  // namespace sgs

@@ -12,6 +12,13 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T>& a, int M, int G, bool diag, int tiles, size_t smem,
                          cudaStream_t st);
 
+// Grant the dynamic shared memory of the plain and traced variants before any launch (so
+// that graph capture never changes kernel attributes).
+template <typename T>
+cudaError_t prepare_sweep(int M, int G, size_t smem, size_t smem_diag);
+
+extern template cudaError_t prepare_sweep<float>(int, int, size_t, size_t);
+extern template cudaError_t prepare_sweep<double>(int, int, size_t, size_t);
 extern template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, bool, int,
                                                 size_t, cudaStream_t);
 extern template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, bool, int,

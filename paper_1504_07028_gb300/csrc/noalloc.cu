@@ -57,12 +57,6 @@ __host__ __device__ inline TableLayout table_layout(int W, int Mf, int Wh) {
   return t;
 }
 
-inline bool smooth7(long n) {
-  for (long r : {2L, 3L, 5L, 7L})
-    while (n % r == 0) n /= r;
-  return n == 1;
-}
-
 // Twiddles (FP64 and FP32), chirp and column coefficients, one thread per index.
 __global__ void k_static_tables(unsigned char* tb, int H, int W, int Mf, int Wh, int blue,
                                 double c) {
@@ -139,16 +133,9 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
     return SEGSALSA_ERR_ARG;
   if (W > 8192) return SEGSALSA_ERR_OOM;
   const int Wh = W / 2 + 1;
-  int Mf = W, blue = 0;
-  if (!smooth7(W)) {
-    if (2L * W - 1 > 8192) return SEGSALSA_ERR_OOM;
-    blue = 1;
-    long m = 2L * W - 1;
-    while (!smooth7(m)) ++m;
-    if (m > 8192) return SEGSALSA_ERR_OOM;
-    Mf = (int)m;
-  }
-  if (Mf > 8192) return SEGSALSA_ERR_OOM;
+  FftPlan<float> pl{};
+  if (!make_fft_plan<float>(W, pl) || pl.Mf > 8192) return SEGSALSA_ERR_OOM;
+  const int Mf = pl.Mf, blue = pl.blue;
   if ((size_t)H * Wh * K > kSpecMaxComplex) return SEGSALSA_ERR_OOM;
   if (table_layout(W, Mf, Wh).end > kTableBytes) return SEGSALSA_ERR_OOM;
   const int CB = 8;
@@ -175,35 +162,20 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
     dc.H = H; dc.W = W; dc.c = c_omega;
   }
 
-  // Stockham radices of Mf (8, 4, 2, then 3, 5, 7)
-  FftPlan<float> pl{};
-  pl.N = W; pl.Mf = Mf; pl.blue = blue;
-  {
-    int m = Mf, s = 0, ns = 1;
-    auto push = [&](int r) { pl.radix[s] = r; pl.ns[s] = ns; ns *= r; ++s; m /= r; };
-    while (m % 8 == 0) push(8);
-    while (m % 4 == 0) push(4);
-    while (m % 2 == 0) push(2);
-    for (int p : {3, 5, 7})
-      while (m % p == 0) push(p);
-    pl.nst = s;
-  }
   pl.tw = reinterpret_cast<const float2*>(tb + TL.tw);
   pl.chirp = reinterpret_cast<const float2*>(tb + TL.chirp);
   pl.bhat = reinterpret_cast<const float2*>(tb + TL.bhat);
 
   const int Q = (K + 1) / 2;
-  int QB = (16 * 512) / Mf;
-  QB = QB < 1 ? 1 : (QB > Q ? Q : QB);
+  const int QB = row_pairs_per_cta(Mf, Q);
   const int nq = (Q + QB - 1) / QB;
-  QB = (Q + nq - 1) / nq;
-  const int need = (Mf * QB + FFT_MAXE - 1) / FFT_MAXE;
-  int rt = (need + 31) / 32 * 32;
-  rt = rt < 64 ? 64 : (rt > 512 ? 512 : rt);
-  const size_t row_smem = sizeof(float2) * (size_t)Mf * QB;
+  const RowLaunch rl = row_launch_config<float>(W, Mf, blue, QB);
+  if (rl.smem > 227 * 1024) return SEGSALSA_ERR_OOM;
 
   RowArgs<float> ra{};
-  ra.H = H; ra.W = W; ra.K = K; ra.Wh = Wh; ra.QB = QB; ra.pl = pl;
+  ra.H = H; ra.W = W; ra.K = K; ra.Wh = Wh; ra.QB = QB; ra.smem_tables = rl.tables; ra.pl = pl;
+  ra.lgB = 0;
+  while ((1 << ra.lgB) < QB) ++ra.lgB;
   ra.src = rhs; ra.S = reinterpret_cast<cplx<float>*>(spec); ra.z = z;
   ColArgs<float> ca{};
   ca.H = H; ca.C = Wh * K; ca.K = K; ca.CB = CB;
@@ -216,16 +188,10 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
   const int col_threads = (2 * CB * ca.NSEG + 31) / 32 * 32;
   const int ncolblk = (Wh * K + CB - 1) / CB;
 
-  if (cudaFuncSetAttribute(k_row_forward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)row_smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_row_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)row_smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_col_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)col_smem) != cudaSuccess)
-    return SEGSALSA_ERR_CUDA;
   const dim3 rg(H, nq);
-  k_row_forward<float><<<rg, rt, row_smem, st>>>(ra);
-  k_col_solve<float><<<ncolblk, col_threads, col_smem, st>>>(ca);
-  k_row_inverse<float><<<rg, rt, row_smem, st>>>(ra);
+  if (launch_row<float>(true, ra, rg, rl, st) != cudaSuccess ||
+      launch_col<float>(ca, ncolblk, col_threads, col_smem, st) != cudaSuccess ||
+      launch_row<float>(false, ra, rg, rl, st) != cudaSuccess)
+    return SEGSALSA_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? SEGSALSA_OK : SEGSALSA_ERR_CUDA;
 }

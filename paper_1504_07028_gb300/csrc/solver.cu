@@ -12,6 +12,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -32,22 +33,6 @@ constexpr int TRACE_CAP = 128;      // device trace records before a flush to th
 static thread_local std::string g_last_error;
 
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-static bool is_smooth7(long n) {
-  for (long r : {2L, 3L, 5L, 7L})
-    while (n % r == 0) n /= r;
-  return n == 1;
-}
-
-static std::vector<int> radices_of(int m) {
-  std::vector<int> r;
-  while (m % 8 == 0) { r.push_back(8); m /= 8; }
-  while (m % 4 == 0) { r.push_back(4); m /= 4; }
-  while (m % 2 == 0) { r.push_back(2); m /= 2; }
-  for (int p : {3, 5, 7})
-    while (m % p == 0) { r.push_back(p); m /= p; }
-  return r;
-}
 
 struct SolverBase {
   virtual ~SolverBase() {}
@@ -119,9 +104,8 @@ struct Plan {
   int H, W, K, M, L, n, G, NC;
   int ntx, nty, THmax, EHmax, EWmax, ntiles;
   size_t sweep_smem, sweep_smem_diag;
-  int Wh, Mf, blue, QB, row_threads, nqblk;
-  std::vector<int> radix;
-  size_t row_smem;
+  int Wh, Mf, blue, QB, nqblk;
+  RowLaunch row;
   int CB, NSEG, col_threads, ncolblk;
   size_t col_smem;
   int nproj_blk, nprior_blk, ngsq_blk;
@@ -150,11 +134,16 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   pl.n = pl.H * pl.W;
   const int K = pl.K, M = pl.M, H = pl.H, W = pl.W;
   pl.G = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-  pl.NC = 256 / pl.G;
+  // columns per tile: 256/G, fewer when a CTA's shared memory (two row stages, the z tile and
+  // the accumulators) would not fit
+  const int cand[] = {16, 12, 8, 6, 4};
+  for (pl.NC = 256 / pl.G; pl.NC > 1; --pl.NC) {
+    const size_t s = sweep_smem_bytes<T>(pl.NC, 16 + 2 * M + 1, pl.NC + 2 * M + 1, pl.G, pl.L, K, true);
+    if (s <= 220 * 1024) break;
+  }
   pl.ntx = (W + pl.NC - 1) / pl.NC;
   // tile height: the largest of {16, 12, 8, 6, 4} that still gives two CTAs per SM (152 SMs);
   // with more than one tile row every tile must be at least 2M+1 rows high
-  const int cand[] = {16, 12, 8, 6, 4};
   pl.THmax = 0;
   int fallback = 0;
   for (int th : cand) {
@@ -167,44 +156,45 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   pl.nty = (H + pl.THmax - 1) / pl.THmax;
   pl.EHmax = pl.THmax + 2 * M + 1;
   pl.EWmax = pl.NC + 2 * M + 1;
-  pl.sweep_smem = sweep_smem_bytes<T>(pl.EHmax, pl.EWmax, pl.G, pl.L, false);
-  pl.sweep_smem_diag = sweep_smem_bytes<T>(pl.EHmax, pl.EWmax, pl.G, pl.L, true);
-  if (pl.sweep_smem_diag > 220 * 1024) { msg = "tile does not fit in shared memory"; return SEGSALSA_ERR_ARG; }
+  pl.sweep_smem = sweep_smem_bytes<T>(pl.NC, pl.EHmax, pl.EWmax, pl.G, pl.L, K, false);
+  pl.sweep_smem_diag = sweep_smem_bytes<T>(pl.NC, pl.EHmax, pl.EWmax, pl.G, pl.L, K, true);
+  if (pl.sweep_smem_diag > 227 * 1024) { msg = "tile does not fit in shared memory"; return SEGSALSA_ERR_ARG; }
   pl.ntiles = pl.ntx * pl.nty;
+  if ((long long)pl.ntiles * pl.EHmax * pl.EWmax * K >= (1LL << 31)) { msg = "image too large for 32-bit partial offsets"; return SEGSALSA_ERR_ARG; }
   if (!build_cover(H, pl.nty, M, M + 1, pl.covY) || !build_cover(W, pl.ntx, M, M + 1, pl.covX)) {
     msg = "image too small for the tiling"; return SEGSALSA_ERR_ARG;
   }
   // row FFT
   pl.Wh = W / 2 + 1;
-  if (is_smooth7(W)) { pl.Mf = W; pl.blue = 0; }
-  else {
-    pl.blue = 1;
-    long m = 2L * W - 1;
-    while (!is_smooth7(m)) ++m;
-    pl.Mf = (int)m;
+  {
+    FftPlan<T> fp{};
+    if (!make_fft_plan<T>(W, fp)) { msg = "no FFT plan for this row length"; return SEGSALSA_ERR_ARG; }
+    pl.Mf = fp.Mf;
+    pl.blue = fp.blue;
   }
-  if (pl.Mf > 16 * 512) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
-  pl.radix = radices_of(pl.Mf);
-  if ((int)pl.radix.size() > FFT_MAXST) { msg = "too many FFT stages"; return SEGSALSA_ERR_ARG; }
+  if (pl.Mf > 8192) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
   const int Q = (K + 1) / 2;
-  pl.QB = std::max(1, std::min(Q, (16 * 512) / pl.Mf));
+  pl.QB = row_pairs_per_cta(pl.Mf, Q, H);
   pl.nqblk = (Q + pl.QB - 1) / pl.QB;
-  pl.QB = (Q + pl.nqblk - 1) / pl.nqblk;  // balance the pair chunks
-  const int need = (pl.Mf * pl.QB + FFT_MAXE - 1) / FFT_MAXE;
-  pl.row_threads = std::min(512, std::max(64, (need + 31) / 32 * 32));
-  pl.row_smem = sizeof(cplx<T>) * (size_t)pl.Mf * pl.QB;
-  // column solve
+  pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB);
+  if (pl.row.smem > 227 * 1024) { msg = "row too long for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
+  // column solve: column blocks of CB complex values, all H rows in shared memory (<= 64 KiB
+  // so that several CTAs share an SM), NSEG segments per column
   pl.CB = sizeof(T) == 4 ? 8 : 4;
-  while ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024 && pl.CB > 1) pl.CB /= 2;
+  while ((size_t)H * pl.CB * sizeof(cplx<T>) > 64 * 1024 && pl.CB > 1) pl.CB /= 2;
   if ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024) { msg = "image too tall for the column solve"; return SEGSALSA_ERR_ARG; }
+  // small images: thinner column blocks so that the grid covers the GPU
+  while (pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 8 * 152) pl.CB /= 2;
   pl.col_smem = (size_t)H * pl.CB * sizeof(cplx<T>);
   const int nseq = 2 * pl.CB;
-  pl.NSEG = std::max(1, std::min(H / 24, 1024 / nseq));
+  // segments of about 8 rows: the serial chain is two warm-ups plus two passes over a segment
+  pl.NSEG = std::max(1, std::min(H / 8, 1024 / nseq));
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
   // diagnostics
-  const int cap = 152 * 8;
-  pl.nproj_blk = std::min(cap, (pl.n + AUX_THREADS - 1) / AUX_THREADS);
+  const int cap = 152 * 2;
+  const int ppb = AUX_THREADS / pl.G;  // pixels per diagnostics block
+  pl.nproj_blk = std::min(cap, (pl.n + ppb - 1) / ppb);
   pl.nprior_blk = pl.nproj_blk;
   pl.ngsq_blk = (int)std::min<long long>(cap, ((long long)pl.n * K + AUX_THREADS - 1) / AUX_THREADS);
   return SEGSALSA_OK;
@@ -229,8 +219,9 @@ struct Buffers {
   int32_t* lab;
   double *dsq, *dproj, *dprior, *dgsq, *dtrace;
   int* flag;
+  int* err;  // set by kernels whose bounded waits gave up
   T* omega;
-  int *covY, *covX;
+  int *covY, *covX, *offX;
   T *beta, *gain, *wfac;
   int* nwarm;
   cplx<T>*tw, *chirp, *bhat;
@@ -240,10 +231,11 @@ template <typename T>
 static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   Carver c{base};
   const size_t nK = (size_t)pl.n * pl.K;
-  b.p = c.take<T>(nK);
+  // p, dloc and d2 are read by 16-byte-rounded bulk copies: 64 bytes of slack after each
+  b.p = c.take<T>(nK + 64 / sizeof(T));
   b.z = c.take<T>(nK);
-  b.dloc = c.take<T>(3 * nK);
-  b.d2 = c.take<T>(2 * (size_t)pl.L * nK);
+  b.dloc = c.take<T>(3 * nK + 64 / sizeof(T));
+  b.d2 = c.take<T>(2 * (size_t)pl.L * nK + 64 / sizeof(T));
   const size_t tslot = (size_t)pl.ntiles * pl.EHmax * pl.EWmax * pl.K;
   b.P = c.take<T>(tslot);
   b.P2 = c.take<T>(tslot);
@@ -258,9 +250,11 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.dgsq = c.take<double>(pl.ngsq_blk);
   b.dtrace = c.take<double>(6 * (size_t)TRACE_CAP);
   b.flag = c.take<int>(1);
+  b.err = c.take<int>(1);
   b.omega = c.take<T>(pl.L);
   b.covY = c.take<int>((size_t)pl.H * MAXCOV);
   b.covX = c.take<int>((size_t)pl.W * MAXCOV);
+  b.offX = c.take<int>((size_t)pl.W * MAXCOV);
   b.beta = c.take<T>(pl.Wh);
   b.gain = c.take<T>(pl.Wh);
   b.wfac = c.take<T>(pl.Wh);
@@ -298,9 +292,22 @@ class Solver : public SolverBase {
   bool profiling = false;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> evs;
   std::vector<cudaEvent_t> evpool;
+  // CUDA graphs of iteration chunks: key (length, traced) -> executable graph and the launch
+  // counts per kind it contains
+  struct Chunk {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches[NKIND] = {0};
+  };
+  std::map<std::pair<int, int>, Chunk> chunks;
+  double* trace_host = nullptr;  // pinned staging for trace records
+  int trace_host_cap = 0;
+  bool use_graphs = true;
 
   ~Solver() override {
     if (st) cudaStreamSynchronize(st);
+    for (auto& kv : chunks)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (trace_host) cudaFreeHost(trace_host);
     for (auto& e : evs) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
     for (auto e : evpool) cudaEventDestroy(e);
     if (own_ws && ws) cudaFree(ws);
@@ -330,6 +337,8 @@ class Solver : public SolverBase {
     carve<T>(pl, reinterpret_cast<char*>(ws), b);
     if (pr->stream) st = reinterpret_cast<cudaStream_t>(pr->stream);
     else { SGS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+    SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
+    SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
     return upload_tables();
   }
 
@@ -338,8 +347,18 @@ class Solver : public SolverBase {
     std::vector<T> om(pl.L);
     for (int j = 0; j < pl.L; ++j) om[j] = (T)omega[j];
     SGS_CUDA(cudaMemcpyAsync(b.omega, om.data(), sizeof(T) * pl.L, cudaMemcpyHostToDevice, st));
+    SGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), st));
     SGS_CUDA(cudaMemcpyAsync(b.covY, pl.covY.data(), sizeof(int) * pl.covY.size(), cudaMemcpyHostToDevice, st));
     SGS_CUDA(cudaMemcpyAsync(b.covX, pl.covX.data(), sizeof(int) * pl.covX.size(), cudaMemcpyHostToDevice, st));
+    {
+      std::vector<int> off(pl.covX.size());
+      for (size_t i = 0; i < off.size(); ++i) {
+        const int cx = pl.covX[i];
+        off[i] = cx < 0 ? -1 : ((cx >> 16) * pl.EHmax * pl.EWmax + (cx & 0xffff)) * pl.K;
+      }
+      SGS_CUDA(cudaMemcpyAsync(b.offX, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, st));
+      SGS_CUDA(cudaStreamSynchronize(st));  // `off` leaves scope
+    }
     // column solve coefficients, per kx: (a + 2c) - c (S + S^-1) = (c/beta)(1 - beta S)(1 - beta/S)
     std::vector<T> beta(Wh), gain(Wh), wfac(Wh);
     std::vector<int> nwarm(Wh);
@@ -422,18 +441,18 @@ class Solver : public SolverBase {
 
   FftPlan<T> fft_plan() const {
     FftPlan<T> f{};
-    f.N = pl.W; f.Mf = pl.Mf; f.blue = pl.blue; f.nst = (int)pl.radix.size();
-    int ns = 1;
-    for (int s = 0; s < f.nst; ++s) { f.radix[s] = pl.radix[s]; f.ns[s] = ns; ns *= pl.radix[s]; }
+    make_fft_plan<T>(pl.W, f);
     f.tw = b.tw; f.chirp = b.chirp; f.bhat = b.bhat;
     return f;
   }
   RowArgs<T> row_args(const T* src, T* zout) const {
     RowArgs<T> a{};
-    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.Wh = pl.Wh; a.QB = pl.QB;
+    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.Wh = pl.Wh; a.QB = pl.QB; a.smem_tables = pl.row.tables;
+    a.lgB = 0;
+    while ((1 << a.lgB) < pl.QB) ++a.lgB;
     a.pl = fft_plan();
     a.src = src; a.P = b.P; a.ntx = pl.ntx; a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
-    a.covY = b.covY; a.covX = b.covX; a.S = b.S; a.z = zout;
+    a.covY = b.covY; a.covX = b.covX; a.offX = b.offX; a.S = b.S; a.z = zout;
     return a;
   }
 
@@ -441,25 +460,23 @@ class Solver : public SolverBase {
   int z_update(const T* src, T* zout) {
     const RowArgs<T> ra = row_args(src, zout);
     const dim3 rg(pl.H, pl.nqblk);
-    SGS_CUDA(cudaFuncSetAttribute(k_row_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.row_smem));
-    SGS_CUDA(cudaFuncSetAttribute(k_row_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.row_smem));
-    SGS_CUDA(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.col_smem));
-    SGS_LAUNCH(KIND_ROWF, (k_row_forward<T><<<rg, pl.row_threads, pl.row_smem, st>>>(ra)));
+    SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
     ColArgs<T> ca{};
     ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG;
     ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
-    SGS_LAUNCH(KIND_COL, (k_col_solve<T><<<pl.ncolblk, pl.col_threads, pl.col_smem, st>>>(ca)));
-    SGS_LAUNCH(KIND_ROWI, (k_row_inverse<T><<<rg, pl.row_threads, pl.row_smem, st>>>(ra)));
+    SGS_CUDA(launch(KIND_COL, [&]() { return launch_col<T>(ca, pl.ncolblk, pl.col_threads, pl.col_smem, st); }));
+    SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row<T>(false, ra, rg, pl.row, st); }));
     return SEGSALSA_OK;
   }
 
   int sweep(bool diag) {
     SweepArgs<T> a{};
-    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.ntx = pl.ntx; a.nty = pl.nty;
+    a.H = pl.H; a.W = pl.W; a.K = pl.K; a.NC = pl.NC; a.ntx = pl.ntx; a.nty = pl.nty;
     a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
     a.z = b.z; a.p = b.p; a.dloc = b.dloc; a.d2 = b.d2; a.P = b.P; a.P2 = b.P2;
     a.diag_sq = b.dsq; a.omega = b.omega;
     a.tau = (T)(lambda / mu); a.mu = (T)mu; a.invK = (T)(1.0 / pl.K); a.sp = sp;
+    a.err = b.err;
     const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
     SGS_CUDA(launch(KIND_SWEEP, [&]() { return launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st); }));
     return SEGSALSA_OK;
@@ -467,18 +484,10 @@ class Solver : public SolverBase {
 
   int diagnostics(int k, int rec) {
     const int n = pl.n, K = pl.K;
-    SGS_LAUNCH(KIND_DIAG, (k_project<T><<<pl.nproj_blk, AUX_THREADS, 0, st>>>(b.z, b.p, b.zp, n, K, b.dproj)));
-    SGS_LAUNCH(KIND_DIAG, (k_prior<T><<<pl.nprior_blk, AUX_THREADS, 0, st>>>(b.zp, b.omega, pl.H, pl.W, K, pl.M, sp, b.dprior)));
-    SGS_LAUNCH(KIND_DIAG, (k_gather_sq<T><<<pl.ngsq_blk, AUX_THREADS, 0, st>>>(b.P2, b.covY, b.covX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq)));
-    SGS_LAUNCH(KIND_DIAG, (k_finalize_trace<<<1, 256, 0, st>>>(b.dsq, pl.ntiles, b.dgsq, pl.ngsq_blk, b.dproj, pl.nproj_blk, b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec)));
-    return SEGSALSA_OK;
-  }
-
-  int flush_trace(int count, double* host, int& written) {
-    if (count <= 0) return SEGSALSA_OK;
-    SGS_CUDA(cudaMemcpyAsync(host + 6 * (size_t)written, b.dtrace, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost, st));
-    SGS_CUDA(cudaStreamSynchronize(st));
-    written += count;
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, b.dproj); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_prior<T>(pl.M, pl.G, pl.nprior_blk, st, b.zp, b.omega, pl.H, pl.W, K, sp, b.dprior); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_gather_sq<T>, dim3(pl.ngsq_blk), dim3(AUX_THREADS), 0, st, (const T*)b.P2, (const int*)b.covY, (const int*)b.covX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(256), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dgsq, pl.ngsq_blk, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
     return SEGSALSA_OK;
   }
 
@@ -524,29 +533,125 @@ class Solver : public SolverBase {
     return SEGSALSA_OK;
   }
 
+  // One iteration launched eagerly: z-update (skipped at k = 0), sweep, and when traced the
+  // diagnostics writing trace slot `rec`.
+  int iteration(bool traced, int rec) {
+    int rc;
+    if (iter > 0) {
+      if ((rc = z_update(rhs_dense ? b.rhsd : nullptr, b.z))) return rc;
+      rhs_dense = false;
+    }
+    if ((rc = sweep(traced))) return rc;
+    if (traced && (rc = diagnostics(iter + 1, rec))) return rc;
+    ++iter;
+    return SEGSALSA_OK;
+  }
+
+  // Executable graph of `len` iterations (k >= 1), the last one traced into slot 0 if `traced`.
+  int get_chunk(int len, bool traced, Chunk*& out) {
+    auto key = std::make_pair(len, traced ? 1 : 0);
+    auto it = chunks.find(key);
+    if (it != chunks.end()) { out = &it->second; return SEGSALSA_OK; }
+    Chunk c;
+    int64_t before[NKIND];
+    for (int i = 0; i < NKIND; ++i) before[i] = nlaunch[i];
+    const int saved_iter = iter;
+    SGS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = SEGSALSA_OK;
+    for (int i = 0; i < len && !rc; ++i) {
+      const bool tr = traced && i == len - 1;
+      if ((rc = z_update(nullptr, b.z))) break;
+      if ((rc = sweep(tr))) break;
+      if (tr) rc = diagnostics(0, 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    iter = saved_iter;
+    for (int i = 0; i < NKIND; ++i) {
+      c.launches[i] = nlaunch[i] - before[i];
+      nlaunch[i] = before[i];
+    }
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(SEGSALSA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SEGSALSA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    out = &chunks.emplace(key, c).first->second;
+    return SEGSALSA_OK;
+  }
+
+  int ensure_trace_host(int n) {
+    if (n <= trace_host_cap) return SEGSALSA_OK;
+    if (trace_host) cudaFreeHost(trace_host);
+    trace_host = nullptr;
+    trace_host_cap = 0;
+    SGS_CUDA(cudaMallocHost(&trace_host, sizeof(double) * 6 * (size_t)n));
+    trace_host_cap = n;
+    return SEGSALSA_OK;
+  }
+
   int solve(int iters, double* trace, int every, int* nrec) override {
     if (!have_probs) return fail(SEGSALSA_ERR_STATE, "solve before set_probs");
     if (iters < 0) return fail(SEGSALSA_ERR_ARG, "iters must be >= 0");
     if (trace && every < 1) return fail(SEGSALSA_ERR_ARG, "trace_every must be >= 1");
-    int pending = 0, written = 0, rc;
-    for (int it = 0; it < iters; ++it) {
-      if (iter > 0) {
-        if ((rc = z_update(rhs_dense ? b.rhsd : nullptr, b.z))) return rc;
-        rhs_dense = false;
-      }
-      const bool tr = trace && (((iter + 1) % every) == 0 || it == iters - 1);
-      if ((rc = sweep(tr))) return rc;
-      if (tr) {
-        if ((rc = diagnostics(iter + 1, pending))) return rc;
-        if (++pending == TRACE_CAP) {
-          if ((rc = flush_trace(pending, trace, written))) return rc;
-          pending = 0;
+    int rc;
+    const int maxrec = trace ? iters / every + 2 : 0;
+    if (trace && (rc = ensure_trace_host(maxrec))) return rc;
+    int written = 0;
+    std::vector<int> rec_k;
+    rec_k.reserve(maxrec);
+    const int untraced_chunk = 16;
+    int it = 0;
+    while (it < iters) {
+      const int left = iters - it;
+      // a whole traced period (or an untraced block) that ends before or at the last iteration
+      const bool can_graph = use_graphs && !profiling && iter >= 1 && !rhs_dense;
+      int len = 0;
+      if (can_graph) {
+        if (trace) {
+          if (iter % every == 0 && every <= left && every > 1) len = every;
+        } else if (left >= untraced_chunk) {
+          len = untraced_chunk;
         }
       }
-      ++iter;
+      if (len > 0) {
+        Chunk* c = nullptr;
+        if ((rc = get_chunk(len, trace != nullptr, c))) return rc;
+        SGS_CUDA(cudaGraphLaunch(c->exec, st));
+        for (int i = 0; i < NKIND; ++i) nlaunch[i] += c->launches[i];
+        iter += len;
+        it += len;
+        if (trace) {
+          SGS_CUDA(cudaMemcpyAsync(trace_host + 6 * (size_t)written, b.dtrace, sizeof(double) * 6,
+                                   cudaMemcpyDeviceToHost, st));
+          rec_k.push_back(iter);
+          ++written;
+        }
+        continue;
+      }
+      const bool tr = trace && (((iter + 1) % every) == 0 || it == iters - 1);
+      if ((rc = iteration(tr, 0))) return rc;
+      ++it;
+      if (tr) {
+        SGS_CUDA(cudaMemcpyAsync(trace_host + 6 * (size_t)written, b.dtrace, sizeof(double) * 6,
+                                 cudaMemcpyDeviceToHost, st));
+        rec_k.push_back(iter);
+        ++written;
+      }
     }
-    if (trace && (rc = flush_trace(pending, trace, written))) return rc;
+    int errflag = 0;
+    SGS_CUDA(cudaMemcpyAsync(&errflag, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SGS_CUDA(cudaStreamSynchronize(st));
+    if (errflag) {
+      cudaMemsetAsync(b.err, 0, sizeof(int), st);
+      return fail(SEGSALSA_ERR_TIMEOUT, "a device-side wait gave up (bounded wait exceeded)");
+    }
+    if (trace) {
+      for (int r = 0; r < written; ++r) {
+        for (int j = 0; j < 6; ++j) trace[6 * r + j] = trace_host[6 * r + j];
+        trace[6 * r] = (double)rec_k[r];
+      }
+    }
     if (nrec) *nrec = written;
     if (trace)
       for (int i = 0; i < 6 * written; ++i)

@@ -29,6 +29,7 @@ namespace sgs {
 template <typename T>
 struct SweepArgs {
   int H, W, K;
+  int NC;                // columns per tile (<= 256 / G)
   int ntx, nty;          // tile grid
   int EHmax, EWmax;      // extents of the P tile slots (tile + halo), in pixels
   const T* z;            // [n][K]
@@ -43,6 +44,7 @@ struct SweepArgs {
   T mu;
   T invK;
   int sp;                // 1, 2, 0 = infinity
+  int* err;              // set to 1 when a bounded wait gives up
 };
 
 // Coefficients of u2 = V A for the prox of tau*||.||_{S_p} at V (R x 2) with Gram
@@ -101,19 +103,100 @@ template <typename T> struct Vec2Of;
 template <> struct Vec2Of<float> { using type = float2; };
 template <> struct Vec2Of<double> { using type = double2; };
 
+// Byte sizes of one pipeline stage (one tile row of d2, dloc and p, each with 16 bytes of
+// alignment slack at both ends), for tiles at most NC pixels wide.
+__host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+template <typename T>
+__host__ __device__ inline void stage_sizes(int NC, int L, int K, size_t& d2b, size_t& dlb,
+                                            size_t& pb) {
+  d2b = al16((size_t)NC * 2 * L * K * sizeof(T) + 32);
+  dlb = al16((size_t)NC * 3 * K * sizeof(T) + 32);
+  pb = al16((size_t)NC * K * sizeof(T) + 32);
+}
+
+// Issue the bulk copies of one tile row (pixels [pix0, pix0 + TW)) into a stage.
+// Each region starts at the 16-byte boundary at or below its first byte; returns nothing,
+// the consumer recomputes the same offsets.
+template <typename T>
+__device__ __forceinline__ void issue_row(const SweepArgs<T>& a, size_t pix0, int TW, int L,
+                                          unsigned char* st, size_t d2b, size_t dlb,
+                                          uint64_t* bar) {
+  const int K = a.K;
+  const char* g0 = reinterpret_cast<const char*>(a.d2) + pix0 * (2 * L * K * sizeof(T));
+  const char* g1 = reinterpret_cast<const char*>(a.dloc) + pix0 * (3 * K * sizeof(T));
+  const char* g2 = reinterpret_cast<const char*>(a.p) + pix0 * (K * sizeof(T));
+  const size_t n0 = (size_t)TW * 2 * L * K * sizeof(T);
+  const size_t n1 = (size_t)TW * 3 * K * sizeof(T);
+  const size_t n2 = (size_t)TW * K * sizeof(T);
+  const char* a0 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g0) & ~uintptr_t(15));
+  const char* a1 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g1) & ~uintptr_t(15));
+  const char* a2 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g2) & ~uintptr_t(15));
+  const uint32_t b0 = (uint32_t)al16((g0 - a0) + n0);
+  const uint32_t b1 = (uint32_t)al16((g1 - a1) + n1);
+  const uint32_t b2 = (uint32_t)al16((g2 - a2) + n2);
+  mbar_arrive_expect_tx(bar, b0 + b1 + b2);
+  bulk_g2s(st, a0, b0, bar);
+  bulk_g2s(st + d2b, a1, b1, bar);
+  bulk_g2s(st + d2b + dlb, a2, b2, bar);
+}
+
+// Deterministic flush of one window row: every thread column c writes its E contributions
+// to exclusive slots (columns c .. c+E-1 of the tile+halo row), the block synchronises, and
+// the owner of each (column, lane) sums the E slots in order s = 0..E-1 and stores the result
+// into the accumulator row (each tile+halo row is flushed exactly once). Slots of idle
+// columns stay zero; the caller synchronises before the slots are written again.
+template <typename T, int G, int E, bool DIAG>
+__device__ __forceinline__ void flush_row(const T (&w)[E], const T (&w2)[DIAG ? E : 1], bool colok,
+                                          int c, int g, T* slots, T* slots2, T* acc, T* acc2,
+                                          int rowbase, int ncols) {
+  constexpr int SW = 256 / G + E - 1;
+  if (colok) {
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      slots[(s * SW + c + s) * G + g] = w[s];
+      if constexpr (DIAG) slots2[(s * SW + c + s) * G + g] = w2[s];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ncols * G; e += blockDim.x) {
+    const int col = e / G, lane = e & (G - 1);
+    T sum = T(0), sum2 = T(0);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      sum += slots[(s * SW + col) * G + lane];
+      if constexpr (DIAG) sum2 += slots2[(s * SW + col) * G + lane];
+    }
+    acc[(rowbase + col) * G + lane] = sum;
+    if constexpr (DIAG) acc2[(rowbase + col) * G + lane] = sum2;
+  }
+}
+
+// Three CTAs per SM for the plain FP32 variant (80 registers, no spills); two otherwise.
+template <typename T, int M, bool DIAG>
+constexpr int sweep_min_blocks() { return (sizeof(T) == 8 || M >= 2 || DIAG) ? 2 : 3; }
+
 template <typename T, int M, int G, bool DIAG>
-__global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(const SweepArgs<T> a) {
   constexpr int L = (2 * M + 1) * (2 * M + 1);
-  constexpr int NC = 256 / G;
   constexpr int E = 2 * M + 2;
   using V2 = typename Vec2Of<T>::type;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);  // 2 stage barriers
+  size_t d2b, dlb, pb;
+  stage_sizes<T>(a.NC, L, a.K, d2b, dlb, pb);
+  const size_t stb = d2b + dlb + pb;
+  unsigned char* stage0 = smem_raw + 128;
   const int slot = a.EHmax * a.EWmax * G;
-  T* zs = reinterpret_cast<T*>(smem_raw);
+  T* zs = reinterpret_cast<T*>(stage0 + 2 * stb);
   T* acc = zs + slot;
   T* acc2 = acc + slot;                 // only used when DIAG
   T* om = acc + (DIAG ? 2 : 1) * slot;  // [L]
+  // flush slots: row contributions of thread column c for tile+halo column c + s live at
+  // slots[(s * SW + c + s) * G + g]; each (s, column) has one writer, owners sum over s
+  constexpr int SW = 256 / G + E - 1;   // columns of a slot row (NC <= 256 / G)
+  T* slots = om + ((L + 3) & ~3);
+  T* slots2 = slots + E * SW * G;       // only used when DIAG
   __shared__ double red32[32];
 
   const int tile = blockIdx.x;
@@ -126,20 +209,47 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
   const int EH = TH + 2 * M + 1, EW = TW + 2 * M + 1;
   const int K = a.K;
 
-  for (int j = threadIdx.x; j < L; j += blockDim.x) om[j] = a.omega[j];
-  for (int idx = threadIdx.x; idx < slot; idx += blockDim.x) {
-    const int g = idx % G;
-    const int e = idx / G;
-    const int ex = e % a.EWmax, ey = e / a.EWmax;
-    T v = T(0);
-    if (g < K && ex < EW && ey < EH) {
-      const int y = wrap_idx(y0 - M + ey, a.H), x = wrap_idx(x0 - M + ex, a.W);
-      v = a.z[((size_t)y * a.W + x) * K + g];
-    }
-    zs[idx] = v;
-    acc[idx] = T(0);
-    if constexpr (DIAG) acc2[idx] = T(0);
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_fence_init();
   }
+  for (int j = threadIdx.x; j < L; j += blockDim.x) om[j] = a.omega[j];
+  for (int j = threadIdx.x; j < (DIAG ? 2 : 1) * E * SW * G; j += blockDim.x) slots[j] = T(0);
+  pdl_wait();  // z, d, p and the partial buffers belong to the previous kernels
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue_row<T>(a, (size_t)y0 * a.W + x0, TW, L, stage0, d2b, dlb, &mbar[0]);
+    if (TH > 1) issue_row<T>(a, (size_t)(y0 + 1) * a.W + x0, TW, L, stage0 + stb, d2b, dlb, &mbar[1]);
+  }
+  // z tile (with halo, periodic) by per-thread async copies; padded classes read as zero
+  {
+    // element idx = (ey * EWmax + ex) * G + g; threads stride by 256 = (256 / G) pixels, so
+    // (ex, ey) advance incrementally (no runtime division in the loop)
+    constexpr int PS = 256 / G;
+    const int g = threadIdx.x & (G - 1);
+    int p = threadIdx.x / G;
+    int ex = p % a.EWmax, ey = p / a.EWmax;
+    for (int idx = threadIdx.x; idx < slot; idx += 256) {
+      const bool v = g < K && ex < EW && ey < EH;
+      const T* src = a.z;
+      if (v) {
+        int y = y0 - M + ey, xx = x0 - M + ex;
+        y += (y < 0) ? a.H : 0;
+        y -= (y >= a.H) ? a.H : 0;
+        xx += (xx < 0) ? a.W : 0;
+        xx -= (xx >= a.W) ? a.W : 0;
+        src = a.z + ((size_t)y * a.W + xx) * K + g;
+      }
+      cp_async_zfill<sizeof(T)>(zs + idx, src, v);
+      acc[idx] = T(0);
+      if constexpr (DIAG) acc2[idx] = T(0);
+      ex += PS;
+      while (ex >= a.EWmax) { ex -= a.EWmax; ++ey; }
+    }
+  }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
 
   const int g = threadIdx.x % G, c = threadIdx.x / G;
@@ -163,22 +273,43 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
   const T tau = a.tau, mu = a.mu;
 
   for (int r = 0; r < TH; ++r) {
-    const size_t pix = (size_t)(y0 + r) * a.W + x;
-    // ---- loads: duals and p of this pixel / class
+    const int sidx = r & 1;
+    const bool ok = mbar_wait_bounded(&mbar[sidx], (uint32_t)((r >> 1) & 1), WAIT_BUDGET_CYCLES);
+    if (__syncthreads_or(!ok)) {
+      // a copy never completed: report, give the other stage a bounded chance, and leave
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, 1);
+        if (r + 1 < TH) mbar_wait_bounded(&mbar[sidx ^ 1], (uint32_t)(((r + 1) >> 1) & 1), WAIT_BUDGET_CYCLES);
+      }
+      return;
+    }
+    // every thread is past row r-1: its stage can take row r+1
+    if (threadIdx.x == 0 && r >= 1 && r + 1 < TH)
+      issue_row<T>(a, (size_t)(y0 + r + 1) * a.W + x0, TW, L, stage0 + (sidx ^ 1) * stb, d2b,
+                   dlb, &mbar[sidx ^ 1]);
+    const size_t pix0 = (size_t)(y0 + r) * a.W + x0;
+    const size_t pix = pix0 + (colok ? c : 0);
+    unsigned char* st = stage0 + sidx * stb;
+    // the consumer's view of the three regions (same 16-byte rounding as issue_row)
+    const uintptr_t q0 = reinterpret_cast<uintptr_t>(a.d2) + pix0 * (2 * L * K * sizeof(T));
+    const uintptr_t q1 = reinterpret_cast<uintptr_t>(a.dloc) + pix0 * (3 * K * sizeof(T));
+    const uintptr_t q2 = reinterpret_cast<uintptr_t>(a.p) + pix0 * (K * sizeof(T));
+    const V2* sd2 = reinterpret_cast<const V2*>(st + (q0 & 15)) + (size_t)c * L * K + g;
+    const T* sdl = reinterpret_cast<const T*>(st + d2b + (q1 & 15)) + (size_t)c * 3 * K + g;
+    const T* sp = reinterpret_cast<const T*>(st + d2b + dlb + (q2 & 15)) + (size_t)c * K + g;
+    // ---- loads: duals and p of this pixel / class (from the staged row)
     V2 dv[L];
-    const V2* d2p = reinterpret_cast<const V2*>(a.d2) + (pix * L) * K + g;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-      if (kok) dv[j] = d2p[(size_t)j * K];
+      if (kok) dv[j] = sd2[j * K];
       else { dv[j].x = T(0); dv[j].y = T(0); }
     }
     T pk = T(0), d1 = T(0), d3 = T(0), d4 = T(0);
     if (kok) {
-      pk = a.p[pix * K + g];
-      const T* dl = a.dloc + pix * 3 * K + g;
-      d1 = dl[0];
-      d3 = dl[K];
-      d4 = dl[2 * K];
+      pk = sp[0];
+      d1 = sdl[0];
+      d3 = sdl[K];
+      d4 = sdl[2 * K];
     }
     // ---- v2 = J z - d2 (eq. 4), from the shared tile
     const T* zc = zs + ((r + M) * EWs + (c + M)) * G + g;
@@ -262,17 +393,9 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
         sq += (n1 - d1) * (n1 - d1) + (n3 - d3) * (n3 - d3) + (n4 - d4) * (n4 - d4);
       }
     }
-    // ---- flush the finished top window row (tile row r + 0 - M + M = r in tile+halo rows)
-    if (colok) {
-      T* ar = acc + (r * EWs + c) * G + g;
-#pragma unroll
-      for (int s = 0; s < E; ++s) atomicAdd(ar + s * G, accW[0][s]);
-      if constexpr (DIAG) {
-        T* ar2 = acc2 + (r * EWs + c) * G + g;
-#pragma unroll
-        for (int s = 0; s < E; ++s) atomicAdd(ar2 + s * G, accW2[0][s]);
-      }
-    }
+    // ---- flush the finished top window row (tile+halo row r), in a fixed summation order
+    flush_row<T, G, E, DIAG>(accW[0], accW2[0], colok, c, g, slots, slots2, acc, acc2,
+                             r * EWs, a.NC + E - 1);
 #pragma unroll
     for (int rr = 0; rr < E - 1; ++rr)
 #pragma unroll
@@ -289,32 +412,29 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
     }
   }
   // remaining window rows: tile+halo rows TH .. TH + 2M
-  if (colok) {
 #pragma unroll
-    for (int rr = 0; rr < E - 1; ++rr) {
-      T* ar = acc + ((TH + rr) * EWs + c) * G + g;
-#pragma unroll
-      for (int s = 0; s < E; ++s) atomicAdd(ar + s * G, accW[rr][s]);
-      if constexpr (DIAG) {
-        T* ar2 = acc2 + ((TH + rr) * EWs + c) * G + g;
-#pragma unroll
-        for (int s = 0; s < E; ++s) atomicAdd(ar2 + s * G, accW2[rr][s]);
-      }
-    }
+  for (int rr = 0; rr < E - 1; ++rr) {
+    __syncthreads();  // the previous flush's owners are done with the slots
+    flush_row<T, G, E, DIAG>(accW[rr], accW2[DIAG ? rr : 0], colok, c, g, slots, slots2, acc,
+                             acc2, (TH + rr) * EWs, a.NC + E - 1);
   }
+  pdl_trigger();
   __syncthreads();
   // ---- write the tile (with halo) partial sums
   {
     T* Pt = a.P + (size_t)tile * a.EHmax * a.EWmax * K;
     T* Pt2 = DIAG ? a.P2 + (size_t)tile * a.EHmax * a.EWmax * K : nullptr;
-    const int tot = EH * EW * K;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      const int k = idx % K;
-      const int e = idx / K;
-      const int ex = e % EW, ey = e / EW;
-      const int so = (ey * EWs + ex);
-      Pt[(size_t)so * K + k] = acc[so * G + k];
-      if constexpr (DIAG) Pt2[(size_t)so * K + k] = acc2[so * G + k];
+    constexpr int PS = 256 / G;
+    const int k = threadIdx.x & (G - 1);
+    int ex = (threadIdx.x / G) % EW, ey = (threadIdx.x / G) / EW;
+    for (; ey < EH;) {
+      if (k < K) {
+        const int so = ey * EWs + ex;
+        Pt[(size_t)so * K + k] = acc[so * G + k];
+        if constexpr (DIAG) Pt2[(size_t)so * K + k] = acc2[so * G + k];
+      }
+      ex += PS;
+      while (ex >= EW) { ex -= EW; ++ey; }
     }
   }
   if constexpr (DIAG) {
@@ -323,15 +443,36 @@ __global__ void __launch_bounds__(256, 2) k_sweep(const SweepArgs<T> a) {
   }
 }
 
+// Largest dynamic shared memory granted so far to each sweep variant.
+template <typename T, int M, int G, bool DIAG>
+struct SweepGrant {
+  static size_t v;
+};
+template <typename T, int M, int G, bool DIAG> size_t SweepGrant<T, M, G, DIAG>::v = 0;
+
+template <typename T, int M, int G, bool DIAG>
+inline cudaError_t grant_sweep(size_t smem) {
+  size_t& g = SweepGrant<T, M, G, DIAG>::v;
+  if (smem <= g) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) g = smem;
+  return e;
+}
+
 template <typename T, int M, int G, bool DIAG>
 inline cudaError_t launch_sweep_inst(const SweepArgs<T>& a, int tiles, size_t smem,
                                      cudaStream_t st) {
-  auto kern = k_sweep<T, M, G, DIAG>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = grant_sweep<T, M, G, DIAG>(smem);
   if (e != cudaSuccess) return e;
-  kern<<<tiles, 256, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_sweep<T, M, G, DIAG>, dim3(tiles), dim3(256), smem, st, a);
+}
+
+template <typename T, int M, int G>
+inline cudaError_t prepare_sweep_inst(size_t smem, size_t smem_diag) {
+  cudaError_t e = grant_sweep<T, M, G, false>(smem);
+  if (e != cudaSuccess) return e;
+  return grant_sweep<T, M, G, true>(smem_diag);
 }
 
 template <typename T, int M, bool DIAG>
@@ -357,10 +498,16 @@ inline cudaError_t launch_sweep_md(const SweepArgs<T>& a, int M, int G, int tile
   return cudaErrorInvalidValue;
 }
 
-// Shared memory of one sweep CTA in bytes.
+// Shared memory of one sweep CTA in bytes: barriers, two row stages, z tile, accumulator(s).
 template <typename T>
-inline size_t sweep_smem_bytes(int EHmax, int EWmax, int G, int L, bool diag) {
-  return sizeof(T) * ((size_t)(diag ? 3 : 2) * EHmax * EWmax * G + (size_t)L);
+inline size_t sweep_smem_bytes(int NC, int EHmax, int EWmax, int G, int L, int K, bool diag) {
+  size_t d2b, dlb, pb;
+  stage_sizes<T>(NC, L, K, d2b, dlb, pb);
+  const int E = EWmax - NC;  // 2M + 1 ... the window width is E + 1 = 2M + 2
+  const size_t slots = (size_t)(E + 1) * (256 / G + E) * G;
+  return 128 + 2 * (d2b + dlb + pb) +
+         sizeof(T) * ((size_t)(diag ? 3 : 2) * EHmax * EWmax * G + (size_t)((L + 3) & ~3) +
+                      (diag ? 2 : 1) * slots);
 }
 
 }  // namespace sgs

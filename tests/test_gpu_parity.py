@@ -261,3 +261,22 @@ def test_invalid_inputs_are_rejected(B):
         s.solve(-1)
     with pytest.raises(TypeError):
         s.set_probs(p.astype(np.float64))
+
+
+def test_graph_replay_matches_eager_launches(B):
+    """solve() replays captured CUDA graphs of whole trace periods; with profiling on it
+    launches every kernel eagerly. Both must give bit-identical iterates and traces."""
+    sc = synth.scene(37, 41, 6, S=5, gap=2.0, noise_std=1.0, wrong_frac=0.05, seed=40)
+    out = []
+    for prof in (False, True):
+        s = _solver(B, 37, 41, 6, 1, 0.5, 1.5, 1.0, 1, "fp32")
+        s.set_profiling(prof)
+        s.set_probs(sc.p.astype(np.float32))
+        tr = s.solve(47, trace_every=10)
+        s.solve(35)                       # untraced: 16-iteration graphs plus a tail
+        out.append((tr, s.get_z(), s.get_iteration()))
+    (t0, z0, k0), (t1, z1, k1) = out
+    assert k0 == k1 == 82
+    assert np.array_equal(t0, t1)
+    assert np.array_equal(z0, z1)
+    assert list(t0[:, 0]) == [10, 20, 30, 40, 47]
