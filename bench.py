@@ -19,6 +19,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -175,22 +176,32 @@ def run_ours(args, rank, world, local_rank):
     sc, cfgs, desc = make_workload(args.workload)
     K, H, W = sc.K, sc.H, sc.W
     n = H * W
+    # the solves of a step are independent: each gets its own handle, stream and host thread,
+    # so their kernels overlap on the GPU (ctypes releases the GIL during the C calls)
     stream = torch.cuda.current_stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in cfgs]
     solvers = []
-    for cfg in cfgs:
+    for cfg, sx in zip(cfgs, streams):
         solvers.append((cfg, B.Solver(B.make_params(
             H, W, K, M=cfg.M, sigma=cfg.sigma, lam=cfg.lam, mu=cfg.mu,
-            schatten_p=cfg.schatten_p, precision="fp32", stream=stream.cuda_stream))))
+            schatten_p=cfg.schatten_p, precision="fp32", stream=sx.cuda_stream))))
     p_dev = torch.from_numpy(sc.p.astype(np.float32)).to(dev)          # (K, H, W)
-    lab_dev = torch.empty((H, W), dtype=torch.int32, device=dev)
+    labs_dev = [torch.empty((H, W), dtype=torch.int32, device=dev) for _ in cfgs]
     iters_per_step = sum(cfg.iters for cfg in cfgs)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    pool = ThreadPoolExecutor(max_workers=len(cfgs))
+
+    def run_all(p_src, labs):
+        def one(i):
+            cfg, s = solvers[i]
+            s.set_probs(p_src)
+            s.solve(cfg.iters, trace_every=10)
+            s.get_labels(labs[i])
+        list(pool.map(one, range(len(solvers))))
 
     def step():
-        for cfg, s in solvers:
-            s.set_probs(p_dev)
-            s.solve(cfg.iters, trace_every=10)
-            s.get_labels(lab_dev)
+        stream.synchronize()                 # p and the L2 flush are ready
+        run_all(p_dev, labs_dev)             # each call returns after its stream finished
 
     for _ in range(args.warmup):
         step()
@@ -235,7 +246,18 @@ def run_ours(args, rank, world, local_rank):
     for _, s in solvers:
         s.reset_stats()
         s.set_profiling(True)
-    prof_ms = float(sum(timed(args.steps)))
+    prof_ms = 0.0
+    for _ in range(args.steps):          # one solve at a time: durations without overlap
+        for i, (cfg, s) in enumerate(solvers):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.set_probs(p_dev)
+            s.solve(cfg.iters, trace_every=10)
+            s.get_labels(labs_dev[i])
+            b.record(stream)
+            b.synchronize()
+            prof_ms += a.elapsed_time(b)
     stats = {}
     for _, s in solvers:
         for kname, (cnt, ms) in s.kernel_stats().items():
@@ -253,16 +275,13 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end through the public API with host buffers (pinned p in, labels out)
     p_host = torch.from_numpy(sc.p.astype(np.float32)).pin_memory()
-    lab_host = torch.empty((H, W), dtype=torch.int32).pin_memory()
+    labs_host = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in cfgs]
     e2e_times = []
     for i in range(max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for cfg, s in solvers:
-            s.set_probs(p_host)
-            s.solve(cfg.iters, trace_every=10)
-            s.get_labels(lab_host)
+        run_all(p_host, labs_host)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_times)
@@ -307,6 +326,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": desc, "H": H, "W": W, "K": K, "iters_per_step": iters_per_step,
+                   "concurrency": f"{len(cfgs)} independent solves per step, one stream and host "
+                                  "thread each",
                    "l2": "flushed between timed steps (256 MB write); the 145x145 working set "
                          "(~45 MB) is L2-resident within a step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -320,7 +341,8 @@ def run_ours(args, rank, world, local_rank):
                      "avg_launch_us": sw_ms / sw_cnt * 1e3},
         "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
         "kernel_timing": ("CUDA events around every launch on the launch stream, in a replay "
-                          f"of the {args.steps} timed steps ({prof_ms:.1f} ms with the events)"),
+                          f"of the {args.steps} timed steps with the solves run one at a time "
+                          f"({prof_ms:.1f} ms with the events)"),
         "dominant_kernel": dom[0],
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "ADMM iter/s", "h2d_bytes_per_step": h2d,
@@ -332,6 +354,7 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     for _, s in solvers:
         s.close()
+    pool.shutdown()
 
 
 def main():

@@ -131,13 +131,12 @@ __device__ __forceinline__ int qdiv(int t, uint32_t mg) {
 // X[n * B + b]: each work item is one radix-R butterfly (in place: every thread reads its
 // inputs, the block synchronises, then writes).
 template <typename T, int R, int MAXE>
-__device__ __forceinline__ void fft_stage(cplx<T>* X, int lgB, int Mf, int Ns, uint32_t mg,
-                                          const cplx<T>* tw) {
+__device__ __forceinline__ void fft_stage(cplx<T>* X, int B, uint32_t mgB, int Mf, int Ns,
+                                          uint32_t mg, const cplx<T>* tw, int S) {
   using C = cplx<T>;
   constexpr int MI = (MAXE + R - 1) / R;
-  const int B = 1 << lgB;
   const int nb = Mf / R;
-  const int items = nb << lgB;
+  const int items = nb * B;
   const int stride = nb / Ns;
   C out[MI][R];
   int base[MI];
@@ -146,18 +145,18 @@ __device__ __forceinline__ void fft_stage(cplx<T>* X, int lgB, int Mf, int Ns, u
     const int it = threadIdx.x + q * blockDim.x;
     base[q] = -1;
     if (it < items) {
-      const int b = it & (B - 1), t = it >> lgB;
+      const int t = qdiv(it, mgB), b = it - t * B;
       const int g = qdiv(t, mg);
       const int j = t - g * Ns;
       C v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = X[((t + r * nb) << lgB) + b];
+      for (int r = 0; r < R; ++r) v[r] = X[(t + r * nb) * S + b];
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * j * stride]);
       Dft<R, C>::run(v);
 #pragma unroll
       for (int r = 0; r < R; ++r) out[q][r] = v[r];
-      base[q] = ((g * Ns * R + j) << lgB) + b;
+      base[q] = (g * Ns * R + j) * S + b;
     }
   }
   __syncthreads();
@@ -165,7 +164,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* X, int lgB, int Mf, int Ns, u
   for (int q = 0; q < MI; ++q) {
     if (base[q] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) X[base[q] + ((r * Ns) << lgB)] = out[q][r];
+      for (int r = 0; r < R; ++r) X[base[q] + r * Ns * S] = out[q][r];
     }
   }
   __syncthreads();
@@ -175,13 +174,12 @@ __device__ __forceinline__ void fft_stage(cplx<T>* X, int lgB, int Mf, int Ns, u
 // sum_r X[t + r nb] w^{r (j s + m nb)} with o = g Ns R + m Ns + j, t = g Ns + j, s = nb / Ns
 // (twiddle and the radix-R DFT root folded into one table index). MAXE outputs per thread.
 template <typename T, int MAXE>
-__device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int lgB, int Mf, int R, int Ns,
-                                                 uint32_t mg_ns, uint32_t mg_nsr,
-                                                 const cplx<T>* tw) {
+__device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int B, uint32_t mgB, int Mf, int R,
+                                                 int Ns, uint32_t mg_ns, uint32_t mg_nsr,
+                                                 const cplx<T>* tw, int S) {
   using C = cplx<T>;
-  const int B = 1 << lgB;
   const int nb = Mf / R;
-  const int items = Mf << lgB;
+  const int items = Mf * B;
   const int s = nb / Ns;
   const int NsR = Ns * R;
   C out[MAXE];
@@ -190,7 +188,7 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int lgB, int Mf, in
     const int it = threadIdx.x + q * blockDim.x;
     out[q] = mkc<T>(T(0), T(0));
     if (it < items) {
-      const int b = it & (B - 1), o = it >> lgB;
+      const int o = qdiv(it, mgB), b = it - o * B;
       const int g = qdiv(o, mg_nsr);
       const int rem = o - g * NsR;
       const int m = qdiv(rem, mg_ns);
@@ -200,9 +198,9 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int lgB, int Mf, in
       step -= (step >= Mf) ? Mf : 0;
       int idx = 0;
       T ax = T(0), ay = T(0);
-      const C* src = X + (t << lgB) + b;
+      const C* src = X + t * S + b;
       for (int r = 0; r < R; ++r) {
-        const C v = src[(r * nb) << lgB];
+        const C v = src[r * nb * S];
         const C w = tw[idx];
         ax += v.x * w.x - v.y * w.y;
         ay += v.x * w.y + v.y * w.x;
@@ -217,7 +215,10 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int lgB, int Mf, in
 #pragma unroll
   for (int q = 0; q < MAXE; ++q) {
     const int it = threadIdx.x + q * blockDim.x;
-    if (it < items) X[it] = out[q];
+    if (it < items) {
+      const int o = qdiv(it, mgB), b = it - o * B;
+      X[o * S + b] = out[q];
+    }
   }
   __syncthreads();
 }
@@ -231,19 +232,21 @@ struct FftTables {
 };
 
 template <typename T, int MAXE>
-__device__ void fft_forward(cplx<T>* X, int lgB, const FftPlan<T>& pl, const cplx<T>* tw) {
+__device__ void fft_forward(cplx<T>* X, int B, uint32_t mgB, const FftPlan<T>& pl,
+                            const cplx<T>* tw, int S = -1) {
+  if (S < 0) S = B;  // element stride (sequences [0, B) interleaved at unit stride)
   for (int s = 0; s < pl.nst; ++s) {
     const int Ns = pl.ns[s];
     const uint32_t mg = pl.mg_ns[s];
     switch (pl.radix[s]) {
-      case 8: fft_stage<T, 8, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
-      case 4: fft_stage<T, 4, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
-      case 2: fft_stage<T, 2, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
-      case 3: fft_stage<T, 3, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
-      case 5: fft_stage<T, 5, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
-      case 7: fft_stage<T, 7, MAXE>(X, lgB, pl.Mf, Ns, mg, tw); break;
+      case 8: fft_stage<T, 8, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 4: fft_stage<T, 4, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 2: fft_stage<T, 2, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 3: fft_stage<T, 3, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 5: fft_stage<T, 5, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 7: fft_stage<T, 7, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
       default:
-        fft_direct_stage<T, MAXE>(X, lgB, pl.Mf, pl.radix[s], Ns, mg, pl.mg_nsr[s], tw);
+        fft_direct_stage<T, MAXE>(X, B, mgB, pl.Mf, pl.radix[s], Ns, mg, pl.mg_nsr[s], tw, S);
         break;
     }
   }
@@ -277,29 +280,30 @@ __device__ inline FftTables<T> load_tables(const FftPlan<T>& pl, cplx<T>* tab) {
 // [N, Mf) need not be). Afterwards X[k*B + b], k < N, holds X_k for the mixed-radix path; for
 // Bluestein the caller reads bluestein_out(k).
 template <typename T, int MAXE>
-__device__ void dft_rows(cplx<T>* X, int lgB, const FftPlan<T>& pl, const FftTables<T>& tb) {
+__device__ void dft_rows(cplx<T>* X, int B, uint32_t mgB, const FftPlan<T>& pl,
+                         const FftTables<T>& tb) {
   if (!pl.blue) {
-    fft_forward<T, MAXE>(X, lgB, pl, tb.tw);
+    fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);
     return;
   }
   // a_n = x_n conj(chirp_n), zero padded
-  for (int i = threadIdx.x; i < (pl.Mf << lgB); i += blockDim.x) {
-    const int n = i >> lgB;
+  for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x) {
+    const int n = qdiv(i, mgB);
     X[i] = (n < pl.N) ? cmulc(X[i], tb.chirp[n]) : mkc<T>(T(0), T(0));
   }
   __syncthreads();
-  fft_forward<T, MAXE>(X, lgB, pl, tb.tw);
-  for (int i = threadIdx.x; i < (pl.Mf << lgB); i += blockDim.x)
-    X[i] = cconj(cmul(X[i], tb.bhat[i >> lgB]));
+  fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);
+  for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x)
+    X[i] = cconj(cmul(X[i], tb.bhat[qdiv(i, mgB)]));
   __syncthreads();
-  fft_forward<T, MAXE>(X, lgB, pl, tb.tw);  // = conj(cyclic convolution)
+  fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);  // = conj(cyclic convolution)
 }
 
 // Value X_k after dft_rows.
 template <typename T>
-__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* X, int lgB, int k, int b,
+__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* X, int B, int k, int b,
                                            const FftPlan<T>& pl, const FftTables<T>& tb) {
-  const cplx<T> v = X[(k << lgB) + b];
+  const cplx<T> v = X[k * B + b];
   if (!pl.blue) return v;
   return cconj(cmul(tb.chirp[k], v));  // conj(chirp_k) * (a * b)_k
 }
@@ -310,6 +314,7 @@ struct RowArgs {
   int H, W, K, Wh;       // Wh = W/2 + 1 stored frequencies
   int QB;                // class pairs per CTA (a power of two)
   int lgB;               // log2(QB)
+  uint32_t mgB;          // ceil(2^32 / QB)
   int smem_tables;       // 1: copy the transform tables to shared memory
   FftPlan<T> pl;
   // source of rhs: dense [n][K] (src != null) or the sweep partials
@@ -364,10 +369,17 @@ __device__ __forceinline__ T gather_row(const T* P, int rb0, int rb1, const int*
 }
 
 // P offset of the row start of vertical cover cy = (tile row << 16 | ext row), -1 if absent.
+__device__ __forceinline__ int cover_row_base_raw(int cy, int ntx, int EHmax, int EWmax, int K) {
+  if (cy < 0) return -1;
+  return (((cy >> 16) * ntx * EHmax) + (cy & 0xffff)) * EWmax * K;
+}
 template <typename T>
 __device__ __forceinline__ int cover_row_base(const RowArgs<T>& a, int cy) {
-  if (cy < 0) return -1;
-  return (((cy >> 16) * a.ntx * a.EHmax) + (cy & 0xffff)) * a.EWmax * a.K;
+  return cover_row_base_raw(cy, a.ntx, a.EHmax, a.EWmax, a.K);
+}
+// ceil(2^32 / d) on the device (d >= 1; 0 encodes d = 1).
+__device__ __forceinline__ uint32_t div_magic_dev(int d) {
+  return d <= 1 ? 0u : (uint32_t)((0x100000000ULL + (unsigned long long)d - 1) / (unsigned long long)d);
 }
 
 // Shared memory of a row-pass CTA: transform buffer, tables, horizontal offset table.
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
     }
   }
   __syncthreads();
-  dft_rows<T, MAXE>(X, a.lgB, a.pl, tb);
+  dft_rows<T, MAXE>(X, B, a.mgB, a.pl, tb);
   pdl_trigger();
   // unpack the two real spectra: A = (X_k + conj X_{N-k})/2, B = (X_k - conj X_{N-k})/(2i)
   for (int i = threadIdx.x; i < a.Wh * B * 2; i += blockDim.x) {
@@ -438,8 +450,8 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
     const int kx = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C u = dft_out<T>(X, a.lgB, kx, qq, a.pl, tb);
-    const C w = dft_out<T>(X, a.lgB, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
+    const C u = dft_out<T>(X, B, kx, qq, a.pl, tb);
+    const C w = dft_out<T>(X, B, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
     C o;
     if (part == 0) { o.x = T(0.5) * (u.x + w.x); o.y = T(0.5) * (u.y - w.y); }
     else           { o.x = T(0.5) * (u.y + w.y); o.y = T(0.5) * (w.x - u.x); }
@@ -505,7 +517,7 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   }
   cp_async_wait_all();
   __syncthreads();
-  dft_rows<T, MAXE>(X, a.lgB, a.pl, tb);
+  dft_rows<T, MAXE>(X, B, a.mgB, a.pl, tb);
   pdl_trigger();
   const T inv = T(1) / T(N);
   for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
@@ -514,7 +526,7 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
     const int x = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C v = dft_out<T>(X, a.lgB, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
+    const C v = dft_out<T>(X, B, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
     a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
   }
 }
@@ -706,6 +718,7 @@ cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem
 template <typename T>
 cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem);
 
+
 #ifdef SGS_FFT_INSTANTIATE
 template <typename T, int MAXE>
 struct RowGrant {
@@ -783,6 +796,7 @@ extern template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, s
 extern template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
 extern template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
 extern template cudaError_t prepare_fft<double>(const RowLaunch&, size_t);
+
 #endif
 
 }  // namespace sgs

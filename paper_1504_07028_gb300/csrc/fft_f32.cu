@@ -6,4 +6,5 @@ namespace sgs {
 template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
 template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
+
 }  // namespace sgs

@@ -6,4 +6,5 @@ namespace sgs {
 template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t);
 template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_fft<double>(const RowLaunch&, size_t);
+
 }  // namespace sgs

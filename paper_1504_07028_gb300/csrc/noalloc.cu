@@ -176,6 +176,7 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
   ra.H = H; ra.W = W; ra.K = K; ra.Wh = Wh; ra.QB = QB; ra.smem_tables = rl.tables; ra.pl = pl;
   ra.lgB = 0;
   while ((1 << ra.lgB) < QB) ++ra.lgB;
+  ra.mgB = div_magic(QB);
   ra.src = rhs; ra.S = reinterpret_cast<cplx<float>*>(spec); ra.z = z;
   ColArgs<float> ca{};
   ca.H = H; ca.C = Wh * K; ca.K = K; ca.CB = CB;

@@ -450,6 +450,7 @@ class Solver : public SolverBase {
     a.H = pl.H; a.W = pl.W; a.K = pl.K; a.Wh = pl.Wh; a.QB = pl.QB; a.smem_tables = pl.row.tables;
     a.lgB = 0;
     while ((1 << a.lgB) < pl.QB) ++a.lgB;
+    a.mgB = div_magic(pl.QB);
     a.pl = fft_plan();
     a.src = src; a.P = b.P; a.ntx = pl.ntx; a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
     a.covY = b.covY; a.covX = b.covX; a.offX = b.offX; a.S = b.S; a.z = zout;
