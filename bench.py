@@ -30,6 +30,22 @@ METRIC = ("ADMM iters/s and Mpixel·class·iter/s at 1e-4 vs FP64; % HBM rooflin
 SP_LIST = (1, 2, np.inf)
 
 
+def _sweep_traffic(workload):
+    """DRAM bytes per sweep launch from the committed ncu summary, or None when the summary is
+    for another workload or the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"sweep_traffic_{workload}_k16.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = "".join(open(os.path.join(ROOT, p)).read() for p in d["source_files"])
+        if hashlib.sha256(src.encode()).hexdigest() != d["source_sha256"]:
+            return None
+        return float(d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"])
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -191,13 +207,21 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     pool = ThreadPoolExecutor(max_workers=len(cfgs))
 
+    if args.profile_run:                     # eager launches (profiling mode), one thread
+        for _, s in solvers:
+            s.set_profiling(True)
+
     def run_all(p_src, labs):
         def one(i):
             cfg, s = solvers[i]
             s.set_probs(p_src)
             s.solve(cfg.iters, trace_every=10)
             s.get_labels(labs[i])
-        list(pool.map(one, range(len(solvers))))
+        if args.profile_run:
+            for i in range(len(solvers)):
+                one(i)
+        else:
+            list(pool.map(one, range(len(solvers))))
 
     def step():
         stream.synchronize()                 # p and the L2 flush are ready
@@ -263,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
         for kname, (cnt, ms) in s.kernel_stats().items():
             c0, m0 = stats.get(kname, (0, 0.0))
             stats[kname] = (c0 + cnt, m0 + ms)
-        s.set_profiling(False)
+        s.set_profiling(args.profile_run)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     sweep_bytes, iter_bytes = solvers[0][1].traffic_model()
     sw_cnt, sw_ms = stats["sweep"]
@@ -336,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": "sweep (fused prox + dual + rhs partials)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_source": peak_kind,
-                     "traffic": None,
+                     "traffic": _sweep_traffic(args.workload),
                      "algorithmic_bytes_per_launch": sweep_bytes,
                      "avg_launch_us": sw_ms / sw_cnt * 1e3},
         "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
@@ -369,6 +393,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64-check", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="for runs under a profiler: eager kernel launches (no CUDA-graph "
+                         "replay) and the solves of a step one after another")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -215,10 +215,11 @@ inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const
   return cudaGetLastError();
 }
 
-// Sum of squares of G^T d, gathered from the tile partials P2 like the row pass does.
+// Sum of squares of G^T d, gathered from the tile partials P2 in the row pass's fixed order
+// (covY: vertical covers per row, offX: per-column tile offsets).
 template <typename T>
 __global__ void __launch_bounds__(AUX_THREADS) k_gather_sq(const T* P2, const int* covY,
-                                                          const int* covX, int H, int W, int K,
+                                                          const int* offX, int H, int W, int K,
                                                           int ntx, int EHmax, int EWmax,
                                                           double* part) {
   __shared__ double red32[32];
@@ -230,16 +231,18 @@ __global__ void __launch_bounds__(AUX_THREADS) k_gather_sq(const T* P2, const in
     const int k = (int)(i % K);
     const size_t pix = i / K;
     const int y = (int)(pix / W), x = (int)(pix % W);
+    const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
+    const int rb0 = c0 < 0 ? -1 : (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
+    const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
+    const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
     T v = T(0);
-    for (int iy = 0; iy < 2; ++iy) {
-      const int cy = covY[2 * y + iy];
-      if (cy < 0) continue;
-      for (int ix = 0; ix < 2; ++ix) {
-        const int cx = covX[2 * x + ix];
-        if (cx < 0) continue;
-        const size_t t = (size_t)(cy >> 16) * ntx + (cx >> 16);
-        v += P2[((t * EHmax + (cy & 0xffff)) * EWmax + (cx & 0xffff)) * K + k];
-      }
+    if (rb0 >= 0) {
+      if (o0 >= 0) v += P2[rb0 + o0 + k];
+      if (o1 >= 0) v += P2[rb0 + o1 + k];
+    }
+    if (rb1 >= 0) {
+      if (o0 >= 0) v += P2[rb1 + o0 + k];
+      if (o1 >= 0) v += P2[rb1 + o1 + k];
     }
     val += v * v;
   }

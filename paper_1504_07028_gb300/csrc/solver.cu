@@ -174,7 +174,10 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   }
   if (pl.Mf > 8192) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
   const int Q = (K + 1) / 2;
-  pl.QB = row_pairs_per_cta(pl.Mf, Q, H);
+  // small images (latency bound): fewer class pairs per CTA so the grid covers the GPU;
+  // larger ones: as many as fit (contiguous 64-byte pixel reads, fewer CTAs)
+  const bool small_image = (long long)H * W < 65536;
+  pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
   pl.nqblk = (Q + pl.QB - 1) / pl.QB;
   pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB);
   if (pl.row.smem > 227 * 1024) { msg = "row too long for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
@@ -184,19 +187,22 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   while ((size_t)H * pl.CB * sizeof(cplx<T>) > 64 * 1024 && pl.CB > 1) pl.CB /= 2;
   if ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024) { msg = "image too tall for the column solve"; return SEGSALSA_ERR_ARG; }
   // small images: thinner column blocks so that the grid covers the GPU
-  while (pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 8 * 152) pl.CB /= 2;
+  while (small_image && pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 8 * 152) pl.CB /= 2;
   pl.col_smem = (size_t)H * pl.CB * sizeof(cplx<T>);
   const int nseq = 2 * pl.CB;
   // segments of about 8 rows: the serial chain is two warm-ups plus two passes over a segment
-  pl.NSEG = std::max(1, std::min(H / 8, 1024 / nseq));
+  // segment length: 8 rows for small images (short serial chains), 32 rows otherwise (the
+  // two warm-up recursions per segment then cost less than the segment itself)
+  pl.NSEG = std::max(1, std::min(H / (small_image ? 8 : 32), 1024 / nseq));
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
   // diagnostics
-  const int cap = 152 * 2;
+  const int cap = 152 * 16;
   const int ppb = AUX_THREADS / pl.G;  // pixels per diagnostics block
-  pl.nproj_blk = std::min(cap, (pl.n + ppb - 1) / ppb);
+  // at least four grid-stride rounds per block, at most 16 blocks per SM
+  pl.nproj_blk = std::max(1, std::min(cap, (pl.n + 4 * ppb - 1) / (4 * ppb)));
   pl.nprior_blk = pl.nproj_blk;
-  pl.ngsq_blk = (int)std::min<long long>(cap, ((long long)pl.n * K + AUX_THREADS - 1) / AUX_THREADS);
+  pl.ngsq_blk = (int)std::max<long long>(1, std::min<long long>(cap, ((long long)pl.n * K + 4 * AUX_THREADS - 1) / (4 * AUX_THREADS)));
   return SEGSALSA_OK;
 }
 
@@ -487,8 +493,8 @@ class Solver : public SolverBase {
     const int n = pl.n, K = pl.K;
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, b.dproj); }));
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_prior<T>(pl.M, pl.G, pl.nprior_blk, st, b.zp, b.omega, pl.H, pl.W, K, sp, b.dprior); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_gather_sq<T>, dim3(pl.ngsq_blk), dim3(AUX_THREADS), 0, st, (const T*)b.P2, (const int*)b.covY, (const int*)b.covX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(256), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dgsq, pl.ngsq_blk, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_gather_sq<T>, dim3(pl.ngsq_blk), dim3(AUX_THREADS), 0, st, (const T*)b.P2, (const int*)b.covY, (const int*)b.offX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(1024), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dgsq, pl.ngsq_blk, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
     return SEGSALSA_OK;
   }
 

@@ -16,10 +16,10 @@
 // The Jacobian stencil reads z from a shared-memory copy of the tile plus its halo
 // ([-M, M+1] around every pixel). J^T w is a scatter: pixel i sends +/- omega_j w to the
 // (2M+2)^2 neighbours i + s_j (+ e_h / e_v). Each thread keeps those sums for the rows it can
-// still touch in a (2M+2)x(2M+2) register window and flushes the finished top row into a
-// shared accumulator over the tile plus halo (shared atomics, 2M+2 per pixel and class).
-// The accumulator tile, halo included, is written to a partials buffer P; the row-FFT pass
-// adds the overlapping tiles when it reads rhs (no global atomics, deterministic).
+// still touch in a (2M+2)x(2M+2) register window; every row step, the finished top window row
+// goes through exclusive shared-memory slots, is summed in a fixed order by the owner of each
+// column and stored as one row of the tile's partials P (tile plus halo). The row-FFT pass
+// adds the overlapping tiles when it reads rhs (no atomics anywhere: deterministic).
 #pragma once
 
 #include "common.cuh"
@@ -142,13 +142,13 @@ __device__ __forceinline__ void issue_row(const SweepArgs<T>& a, size_t pix0, in
 
 // Deterministic flush of one window row: every thread column c writes its E contributions
 // to exclusive slots (columns c .. c+E-1 of the tile+halo row), the block synchronises, and
-// the owner of each (column, lane) sums the E slots in order s = 0..E-1 and stores the result
-// into the accumulator row (each tile+halo row is flushed exactly once). Slots of idle
-// columns stay zero; the caller synchronises before the slots are written again.
+// the owner of each (column, class) sums the E slots in order s = 0..E-1 and stores the result
+// straight into row `ey` of the tile's partials (each tile+halo row is flushed exactly once).
+// Slots of idle columns stay zero; the caller synchronises before the slots are reused.
 template <typename T, int G, int E, bool DIAG>
 __device__ __forceinline__ void flush_row(const T (&w)[E], const T (&w2)[DIAG ? E : 1], bool colok,
-                                          int c, int g, T* slots, T* slots2, T* acc, T* acc2,
-                                          int rowbase, int ncols) {
+                                          int c, int g, T* slots, T* slots2, T* Pt, T* Pt2,
+                                          int ey, int EWmax, int EW, int K) {
   constexpr int SW = 256 / G + E - 1;
   if (colok) {
 #pragma unroll
@@ -158,16 +158,18 @@ __device__ __forceinline__ void flush_row(const T (&w)[E], const T (&w2)[DIAG ? 
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < ncols * G; e += blockDim.x) {
+  for (int e = threadIdx.x; e < EW * G; e += blockDim.x) {
     const int col = e / G, lane = e & (G - 1);
+    if (lane >= K) continue;
     T sum = T(0), sum2 = T(0);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
       sum += slots[(s * SW + col) * G + lane];
       if constexpr (DIAG) sum2 += slots2[(s * SW + col) * G + lane];
     }
-    acc[(rowbase + col) * G + lane] = sum;
-    if constexpr (DIAG) acc2[(rowbase + col) * G + lane] = sum2;
+    const size_t o = ((size_t)ey * EWmax + col) * K + lane;
+    Pt[o] = sum;
+    if constexpr (DIAG) Pt2[o] = sum2;
   }
 }
 
@@ -189,9 +191,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
   unsigned char* stage0 = smem_raw + 128;
   const int slot = a.EHmax * a.EWmax * G;
   T* zs = reinterpret_cast<T*>(stage0 + 2 * stb);
-  T* acc = zs + slot;
-  T* acc2 = acc + slot;                 // only used when DIAG
-  T* om = acc + (DIAG ? 2 : 1) * slot;  // [L]
+  T* om = zs + slot;                    // [L]
   // flush slots: row contributions of thread column c for tile+halo column c + s live at
   // slots[(s * SW + c + s) * G + g]; each (s, column) has one writer, owners sum over s
   constexpr int SW = 256 / G + E - 1;   // columns of a slot row (NC <= 256 / G)
@@ -208,6 +208,9 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
   const int TH = y1 - y0, TW = x1 - x0;
   const int EH = TH + 2 * M + 1, EW = TW + 2 * M + 1;
   const int K = a.K;
+  (void)EH;
+  T* Pt = a.P + (size_t)tile * a.EHmax * a.EWmax * K;   // this tile's partials (tile + halo)
+  T* Pt2 = DIAG ? a.P2 + (size_t)tile * a.EHmax * a.EWmax * K : nullptr;
 
   if (threadIdx.x == 0) {
     mbar_init(&mbar[0], 1);
@@ -242,8 +245,6 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
         src = a.z + ((size_t)y * a.W + xx) * K + g;
       }
       cp_async_zfill<sizeof(T)>(zs + idx, src, v);
-      acc[idx] = T(0);
-      if constexpr (DIAG) acc2[idx] = T(0);
       ex += PS;
       while (ex >= a.EWmax) { ex -= a.EWmax; ++ey; }
     }
@@ -394,8 +395,8 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
       }
     }
     // ---- flush the finished top window row (tile+halo row r), in a fixed summation order
-    flush_row<T, G, E, DIAG>(accW[0], accW2[0], colok, c, g, slots, slots2, acc, acc2,
-                             r * EWs, a.NC + E - 1);
+    flush_row<T, G, E, DIAG>(accW[0], accW2[0], colok, c, g, slots, slots2, Pt, Pt2, r, EWs,
+                             EW, K);
 #pragma unroll
     for (int rr = 0; rr < E - 1; ++rr)
 #pragma unroll
@@ -412,30 +413,12 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     }
   }
   // remaining window rows: tile+halo rows TH .. TH + 2M
+  pdl_trigger();
 #pragma unroll
   for (int rr = 0; rr < E - 1; ++rr) {
     __syncthreads();  // the previous flush's owners are done with the slots
-    flush_row<T, G, E, DIAG>(accW[rr], accW2[DIAG ? rr : 0], colok, c, g, slots, slots2, acc,
-                             acc2, (TH + rr) * EWs, a.NC + E - 1);
-  }
-  pdl_trigger();
-  __syncthreads();
-  // ---- write the tile (with halo) partial sums
-  {
-    T* Pt = a.P + (size_t)tile * a.EHmax * a.EWmax * K;
-    T* Pt2 = DIAG ? a.P2 + (size_t)tile * a.EHmax * a.EWmax * K : nullptr;
-    constexpr int PS = 256 / G;
-    const int k = threadIdx.x & (G - 1);
-    int ex = (threadIdx.x / G) % EW, ey = (threadIdx.x / G) / EW;
-    for (; ey < EH;) {
-      if (k < K) {
-        const int so = ey * EWs + ex;
-        Pt[(size_t)so * K + k] = acc[so * G + k];
-        if constexpr (DIAG) Pt2[(size_t)so * K + k] = acc2[so * G + k];
-      }
-      ex += PS;
-      while (ex >= EW) { ex -= EW; ++ey; }
-    }
+    flush_row<T, G, E, DIAG>(accW[rr], accW2[DIAG ? rr : 0], colok, c, g, slots, slots2, Pt, Pt2,
+                             TH + rr, EWs, EW, K);
   }
   if constexpr (DIAG) {
     const double t = block_sum_d((double)sq, red32);
@@ -506,7 +489,7 @@ inline size_t sweep_smem_bytes(int NC, int EHmax, int EWmax, int G, int L, int K
   const int E = EWmax - NC;  // 2M + 1 ... the window width is E + 1 = 2M + 2
   const size_t slots = (size_t)(E + 1) * (256 / G + E) * G;
   return 128 + 2 * (d2b + dlb + pb) +
-         sizeof(T) * ((size_t)(diag ? 3 : 2) * EHmax * EWmax * G + (size_t)((L + 3) & ~3) +
+         sizeof(T) * ((size_t)EHmax * EWmax * G + (size_t)((L + 3) & ~3) +
                       (diag ? 2 : 1) * slots);
 }
 
