@@ -46,6 +46,24 @@ def _sweep_traffic(workload):
         return None
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest `value` over all ranks (the slowest replica defines the step time); the
+    identity when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    timed by the slowest rank."""
+    return units_per_rank * world / seconds_max
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -257,11 +275,7 @@ def run_ours(args, rank, world, local_rank):
     times = timed(args.steps)
     barrier()
     ck = clocks.stop()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dev)
     launches = 0
     for _, s in solvers:
         launches += sum(c for c, _ in s.kernel_stats().values())
@@ -293,8 +307,7 @@ def run_ours(args, rank, world, local_rank):
     sw_cnt, sw_ms = stats["sweep"]
     hbm_peak, peak_kind = _peaks()
     achieved = sweep_bytes / (sw_ms / sw_cnt * 1e-3) / 1e9
-    total_iters = iters_per_step * args.steps * world
-    value = total_iters / (total_ms * 1e-3)
+    value = whole_job_rate(iters_per_step * args.steps, world, total_ms * 1e-3)
     mpix = value * n * K / 1e6
 
     # ---- end to end through the public API with host buffers (pinned p in, labels out)
@@ -308,12 +321,8 @@ def run_ours(args, rank, world, local_rank):
         run_all(p_host, labs_host)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = iters_per_step * len(e2e_times) * world / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_times), dev)
+    e2e_value = whole_job_rate(iters_per_step * len(e2e_times), world, e2e_s)
     h2d = 4 * n * K * len(solvers)
     d2h = 4 * n * len(solvers) + sum(48 * (cfg.iters // 10 + 1) for cfg, _ in solvers)
 
