@@ -25,6 +25,8 @@
  *  - Device work runs on the handle's stream: the stream given at creation (borrowed, never
  *    destroyed) or a stream the library creates. Calls return after their work has completed
  *    on that stream unless stated otherwise.
+ *  - Device-memory arguments must be ready when the call is made: the handle's stream does not
+ *    wait for work the caller queued on other streams (synchronize or order them first).
  *  - A handle is not thread-safe; separate handles are independent.
  *  - Periodic boundary conditions and forward differences throughout (the cyclic
  *    convolutions of Sec. 4).
@@ -172,6 +174,90 @@ int segsalsa_str_reset_stats(segsalsa_str_t* h);
  * minimum traffic model: every array read or written once, no halo or pass overhead). */
 int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
                                double* iteration_bytes);
+
+/* ------------------------------------------------------------------------------------------
+ * Tiling and batches.
+ *
+ * The paper notes that the whole iteration is per-pixel or per-class independent work apart
+ * from the cyclic convolutions (Sec. 4), so many images can share the GPU. A batch runs every
+ * image's SALSA iterations (12)-(14) inside one CUDA graph per chunk of iterations: each image's
+ * kernels form a chain and the chains of different images run concurrently.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Work decomposition of one image. Zero in a field selects the library's default for it. Any
+ * tiling gives the same iterates up to the summation order of the rhs partials (FP rounding).
+ *   tile_rows   : height of a fused-sweep tile, 4..32 (rounded so that tiles are >= 2M+1 rows)
+ *   row_pairs   : class pairs per row-transform CTA, a power of two (capped at what fits)
+ *   col_block   : frequency columns per column-solve CTA, a power of two 1..8
+ *   row_threads : target threads of a row-transform CTA, 64..1024 (rounded down to a power
+ *                 of two; a CTA gets more when a thread would hold over 16 values)
+ *   col_rows    : rows per segment of the column recursions, 2..4096 */
+typedef struct {
+  int32_t tile_rows;
+  int32_t row_pairs;
+  int32_t col_block;
+  int32_t row_threads;
+  int32_t col_rows;
+} segsalsa_str_tiling;
+
+/* create / workspace_bytes with an explicit tiling (NULL = defaults, same as the plain calls).
+ * SEGSALSA_ERR_ARG if a tiling field is out of range or the tile does not fit on chip. */
+int segsalsa_str_workspace_bytes_tiled(const segsalsa_str_params* params,
+                                       const segsalsa_str_tiling* tiling, size_t* bytes);
+int segsalsa_str_create_tiled(const segsalsa_str_params* params, const segsalsa_str_tiling* tiling,
+                              void* workspace, size_t workspace_bytes, segsalsa_str_t** out);
+/* The tiling a handle runs with (defaults resolved). */
+int segsalsa_str_get_tiling(const segsalsa_str_t* h, segsalsa_str_tiling* out);
+
+typedef struct segsalsa_str_batch segsalsa_str_batch_t; /* opaque; owned by the library */
+
+/* Create a batch of n_images >= 1 independent problems (7) of any size, K, M, p and precision.
+ * params[i].stream must be NULL (each image gets a library stream; the graphs run on
+ * `stream`, a borrowed cudaStream_t, or a library stream when NULL). tiling (nullable) holds
+ * n_images entries; when NULL each image takes the tiling that segsalsa_str_batch_autotune
+ * chose for its class (precision, M, K, size class floor(log2(H W) / 2)) earlier in this
+ * process, else the defaults. Device memory: the sum of the images' workspace_bytes. */
+int segsalsa_str_batch_create(int32_t n_images, const segsalsa_str_params* params,
+                              const segsalsa_str_tiling* tiling, void* stream,
+                              segsalsa_str_batch_t** out);
+
+/* Borrowed handle of image i (0 <= i < n_images), valid until batch_destroy. Every
+ * single-image call works on it: set_probs, solve (this image alone), get_labels, get_z,
+ * get_state / set_state, linear_solve. Do not destroy it. */
+int segsalsa_str_batch_image(segsalsa_str_batch_t* b, int32_t i, segsalsa_str_t** h);
+
+/* Run `iters` >= 0 SALSA iterations on every image (each continues from its own state; every
+ * image needs set_probs first, else SEGSALSA_ERR_STATE). Returns when all are done. Each image
+ * ends exactly where `iters` single-image iterations (segsalsa_str_solve with no trace) on its
+ * handle would, bit for bit. SEGSALSA_ERR_TIMEOUT if a device-side bounded wait gave up. */
+int segsalsa_str_batch_solve(segsalsa_str_batch_t* b, int32_t iters);
+
+/* Project-written autotuner. Groups the images by class (see batch_create), and for each
+ * class, largest total work first, times `trial_iters` >= 1 batch iterations for every
+ * candidate tiling of that class while the other classes keep their current tiling, keeping
+ * the fastest (candidates: tile_rows 4..32, then row_pairs, col_block, row_threads and
+ * col_rows in turn). The lane count
+ * is tuned first the same way (4, 8, 16, 32, n_images). The choice is
+ * stored per class in a process-wide cache (used by later batch_create calls with tiling ==
+ * NULL) and written to chosen[i] (nullable, n_images entries). The images are rebuilt with
+ * the chosen tiling: their state is reset, so call set_probs (again) afterwards. */
+int segsalsa_str_batch_autotune(segsalsa_str_batch_t* b, int32_t trial_iters,
+                                segsalsa_str_tiling* chosen);
+
+/* Lanes: the batch's concurrent chains of images (streams forked from and joined to the
+ * master stream inside each graph). Images are assigned to lanes longest-work-first so that
+ * the lanes carry similar work; the images of one lane run one after the other. Default
+ * min(n_images, 16); the autotuner also picks it. 1 <= lanes (capped at n_images). */
+int segsalsa_str_batch_set_lanes(segsalsa_str_batch_t* b, int32_t lanes);
+int segsalsa_str_batch_get_lanes(const segsalsa_str_batch_t* b, int32_t* lanes);
+
+/* Release the batch, its images and everything the library allocated for it. NULL is a
+ * no-op. */
+void segsalsa_str_batch_destroy(segsalsa_str_batch_t* b);
+
+/* Message of the last failed batch call on `b` ("" if none); for b == NULL, the last failure
+ * of segsalsa_str_batch_create in this thread. */
+const char* segsalsa_str_batch_last_error(const segsalsa_str_batch_t* b);
 
 /* Release the handle and everything the library allocated for it. NULL is a no-op. */
 void segsalsa_str_destroy(segsalsa_str_t* h);

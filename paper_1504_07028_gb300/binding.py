@@ -36,6 +36,10 @@ SYMBOLS = (
     "segsalsa_str_linear_solve", "segsalsa_str_set_profiling", "segsalsa_str_kernel_stats",
     "segsalsa_str_reset_stats", "segsalsa_str_traffic_model", "segsalsa_str_destroy",
     "segsalsa_str_last_error", "segsalsa_str_linear_solve_static",
+    "segsalsa_str_workspace_bytes_tiled", "segsalsa_str_create_tiled", "segsalsa_str_get_tiling",
+    "segsalsa_str_batch_create", "segsalsa_str_batch_image", "segsalsa_str_batch_solve",
+    "segsalsa_str_batch_autotune", "segsalsa_str_batch_set_lanes", "segsalsa_str_batch_get_lanes",
+    "segsalsa_str_batch_destroy", "segsalsa_str_batch_last_error",
 )
 
 
@@ -46,6 +50,21 @@ class Params(C.Structure):
         ("mu", C.c_double), ("schatten_p", C.c_int32), ("precision", C.c_int32),
         ("stream", C.c_void_p),
     ]
+
+
+class Tiling(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("row_pairs", C.c_int32), ("col_block", C.c_int32),
+                ("row_threads", C.c_int32), ("col_rows", C.c_int32)]
+
+    def as_tuple(self):
+        return (self.tile_rows, self.row_pairs, self.col_block, self.row_threads, self.col_rows)
+
+
+def make_tiling(tile_rows=0, row_pairs=0, col_block=0, row_threads=0, col_rows=0) -> Tiling:
+    t = Tiling()
+    t.tile_rows, t.row_pairs, t.col_block = int(tile_rows), int(row_pairs), int(col_block)
+    t.row_threads, t.col_rows = int(row_threads), int(col_rows)
+    return t
 
 
 class SegsalsaError(RuntimeError):
@@ -89,6 +108,20 @@ def load(path: str | None = None):
         "segsalsa_str_destroy": (None, [vp]),
         "segsalsa_str_last_error": (C.c_char_p, [vp]),
         "segsalsa_str_linear_solve_static": (C.c_int, [vp, vp, i32, i32, i32, C.c_double, vp]),
+        "segsalsa_str_workspace_bytes_tiled": (C.c_int, [C.POINTER(Params), C.POINTER(Tiling),
+                                                         C.POINTER(C.c_size_t)]),
+        "segsalsa_str_create_tiled": (C.c_int, [C.POINTER(Params), C.POINTER(Tiling), vp,
+                                                C.c_size_t, C.POINTER(vp)]),
+        "segsalsa_str_get_tiling": (C.c_int, [vp, C.POINTER(Tiling)]),
+        "segsalsa_str_batch_create": (C.c_int, [i32, C.POINTER(Params), C.POINTER(Tiling), vp,
+                                                C.POINTER(vp)]),
+        "segsalsa_str_batch_image": (C.c_int, [vp, i32, C.POINTER(vp)]),
+        "segsalsa_str_batch_solve": (C.c_int, [vp, i32]),
+        "segsalsa_str_batch_autotune": (C.c_int, [vp, i32, C.POINTER(Tiling)]),
+        "segsalsa_str_batch_set_lanes": (C.c_int, [vp, i32]),
+        "segsalsa_str_batch_get_lanes": (C.c_int, [vp, C.POINTER(i32)]),
+        "segsalsa_str_batch_destroy": (None, [vp]),
+        "segsalsa_str_batch_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -134,12 +167,25 @@ def segsalsa_str_workspace_bytes(params: Params) -> int:
     return n.value
 
 
-def segsalsa_str_create(params: Params, workspace_ptr: int | None = None, workspace_bytes: int = 0):
+def segsalsa_str_create(params: Params, workspace_ptr: int | None = None, workspace_bytes: int = 0,
+                        tiling: Tiling | None = None):
     lib = load()
     h = C.c_void_p()
-    _check(lib, None, lib.segsalsa_str_create(C.byref(params), workspace_ptr, workspace_bytes,
-                                              C.byref(h)))
+    if tiling is None:
+        rc = lib.segsalsa_str_create(C.byref(params), workspace_ptr, workspace_bytes, C.byref(h))
+    else:
+        rc = lib.segsalsa_str_create_tiled(C.byref(params), C.byref(tiling), workspace_ptr,
+                                           workspace_bytes, C.byref(h))
+    _check(lib, None, rc)
     return h
+
+
+def segsalsa_str_workspace_bytes_tiled(params: Params, tiling: Tiling | None) -> int:
+    lib = load()
+    n = C.c_size_t(0)
+    _check(lib, None, lib.segsalsa_str_workspace_bytes_tiled(
+        C.byref(params), C.byref(tiling) if tiling is not None else None, C.byref(n)))
+    return n.value
 
 
 def segsalsa_str_destroy(h):
@@ -187,22 +233,34 @@ def make_params(H, W, K, M=1, sigma=0.5, lam=1.5, mu=1.0, schatten_p=1, precisio
 class Solver:
     """One solver handle (wraps segsalsa_str_*). Arrays: numpy (host) or torch (device)."""
 
-    def __init__(self, params: Params, workspace=None):
+    def __init__(self, params: Params, workspace=None, tiling: Tiling | None = None,
+                 _borrowed=None):
         self.lib = load()
         self.params = params
         self.dtype = np.float64 if params.precision == SEGSALSA_FP64 else np.float32
         self.H, self.W, self.K, self.M = params.H, params.W, params.K, params.M
         self.L = (2 * self.M + 1) ** 2
         self._ws = workspace  # keep the caller's memory alive
+        self._owned = _borrowed is None
+        if _borrowed is not None:
+            self.h = _borrowed
+            return
         ptr, nbytes = (None, 0)
         if workspace is not None:
             ptr, nbytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
-        self.h = segsalsa_str_create(params, ptr, nbytes)
+        self.h = segsalsa_str_create(params, ptr, nbytes, tiling)
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.segsalsa_str_destroy(self.h)
+            if self._owned:
+                self.lib.segsalsa_str_destroy(self.h)
             self.h = None
+
+    # segsalsa_str_get_tiling
+    def tiling(self) -> tuple:
+        t = Tiling()
+        self._c(self.lib.segsalsa_str_get_tiling(self.h, C.byref(t)))
+        return t.as_tuple()
 
     def __del__(self):
         try:
@@ -300,3 +358,68 @@ class Solver:
         a, b = C.c_double(0), C.c_double(0)
         self._c(self.lib.segsalsa_str_traffic_model(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+class Batch:
+    """A batch of independent images (wraps segsalsa_str_batch_*). `params` is a list of
+    Params (stream NULL); `tilings` an optional list of Tiling. image(i) gives a borrowed
+    Solver view of image i for set_probs / get_labels / get_z / get_state."""
+
+    def __init__(self, params: list, tilings: list | None = None, stream=None):
+        self.lib = load()
+        n = len(params)
+        self._params = (Params * n)(*params)
+        self._keep = params  # the weights arrays referenced by the Params
+        tl = None
+        if tilings is not None:
+            if len(tilings) != n:
+                raise ValueError("one tiling per image")
+            tl = (Tiling * n)(*tilings)
+        self.b = C.c_void_p()
+        rc = self.lib.segsalsa_str_batch_create(n, self._params, tl, stream, C.byref(self.b))
+        if rc != SEGSALSA_OK:
+            raise SegsalsaError(rc, self.lib.segsalsa_str_batch_last_error(None).decode())
+        self.n = n
+        self.images = []
+        for i in range(n):
+            h = C.c_void_p()
+            self._c(self.lib.segsalsa_str_batch_image(self.b, i, C.byref(h)))
+            self.images.append(Solver(params[i], _borrowed=h))
+
+    def _c(self, rc):
+        if rc != SEGSALSA_OK:
+            raise SegsalsaError(rc, self.lib.segsalsa_str_batch_last_error(self.b).decode())
+
+    def image(self, i: int) -> Solver:
+        return self.images[i]
+
+    # segsalsa_str_batch_solve
+    def solve(self, iters: int):
+        self._c(self.lib.segsalsa_str_batch_solve(self.b, int(iters)))
+
+    # segsalsa_str_batch_autotune
+    def autotune(self, trial_iters: int = 4) -> list:
+        out = (Tiling * self.n)()
+        self._c(self.lib.segsalsa_str_batch_autotune(self.b, int(trial_iters), out))
+        return [t.as_tuple() for t in out]
+
+    def set_lanes(self, lanes: int):
+        self._c(self.lib.segsalsa_str_batch_set_lanes(self.b, int(lanes)))
+
+    def lanes(self) -> int:
+        v = C.c_int32(0)
+        self._c(self.lib.segsalsa_str_batch_get_lanes(self.b, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            for s in self.images:
+                s.h = None
+            self.lib.segsalsa_str_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

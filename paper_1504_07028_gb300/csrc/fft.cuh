@@ -686,11 +686,11 @@ inline bool make_fft_plan(int N, FftPlan<T>& pl) {
 }
 
 template <typename T>
-inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB) {
+inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_threads = 1024) {
   RowLaunch r{};
   const int elems = Mf * QB;
   r.maxe = 1;
-  while (r.maxe < 16 && (elems + r.maxe - 1) / r.maxe > 1024) r.maxe *= 2;
+  while (r.maxe < 16 && (elems + r.maxe - 1) / r.maxe > target_threads) r.maxe *= 2;
   int t = (elems + r.maxe - 1) / r.maxe;
   t = (t + 31) / 32 * 32;
   r.threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);

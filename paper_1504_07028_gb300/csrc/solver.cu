@@ -14,6 +14,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -50,6 +52,16 @@ struct SolverBase {
   virtual int kernel_stats(int64_t* launches, double* ms) = 0;
   virtual int reset_stats() = 0;
   virtual int traffic(double* sweep, double* iter) const = 0;
+  virtual segsalsa_str_tiling tiling() const = 0;
+  // batch support: every call below enqueues on the given stream and never synchronizes
+  virtual bool ready() const = 0;                      // set_probs has been called
+  virtual bool graphable() const = 0;                  // next iteration is a plain one (k >= 1)
+  virtual int enqueue_iterations(int len, cudaStream_t s) = 0;  // launches only; state unchanged
+  virtual void advance(int len) = 0;                   // account for `len` enqueued iterations
+  virtual int enqueue_eager_iteration(cudaStream_t s) = 0;       // one iteration, state advanced
+  virtual int enqueue_read_err(int* host, cudaStream_t s) = 0;   // copy the device error flag
+  virtual int clear_err(cudaStream_t s) = 0;
+  virtual void invalidate() = 0;                       // forget p and the iterates
   int fail(int code, const std::string& m) { err = m; return code; }
 };
 
@@ -107,6 +119,7 @@ struct Plan {
   int Wh, Mf, blue, QB, nqblk;
   RowLaunch row;
   int CB, NSEG, col_threads, ncolblk;
+  int row_threads, col_rows;   // target threads of a row-pass CTA; rows per column segment
   size_t col_smem;
   int nproj_blk, nprior_blk, ngsq_blk;
   std::vector<int> covY, covX;  // [H][MAXCOV], [W][MAXCOV]
@@ -127,8 +140,27 @@ static bool build_cover(int N, int ntile, int lo, int hi, std::vector<int>& cov)
   return true;
 }
 
+// Tiling fields accepted by the *_tiled calls (0 = default).
+static int check_tiling(const segsalsa_str_tiling* t, std::string& msg) {
+  if (!t) return SEGSALSA_OK;
+  if (t->tile_rows && (t->tile_rows < 4 || t->tile_rows > 32)) { msg = "tile_rows must be 0 or 4..32"; return SEGSALSA_ERR_ARG; }
+  if (t->row_pairs < 0 || t->row_pairs > 64) { msg = "row_pairs must be 0..64"; return SEGSALSA_ERR_ARG; }
+  if (t->col_block < 0 || t->col_block > 8) { msg = "col_block must be 0..8"; return SEGSALSA_ERR_ARG; }
+  if (t->row_threads && (t->row_threads < 64 || t->row_threads > 1024)) { msg = "row_threads must be 0 or 64..1024"; return SEGSALSA_ERR_ARG; }
+  if (t->col_rows && (t->col_rows < 2 || t->col_rows > 4096)) { msg = "col_rows must be 0 or 2..4096"; return SEGSALSA_ERR_ARG; }
+  return SEGSALSA_OK;
+}
+
+static int floor_pow2(int v) {
+  int r = 1;
+  while (2 * r <= v) r *= 2;
+  return r;
+}
+
 template <typename T>
-static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) {
+static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
+                     const segsalsa_str_tiling* tl = nullptr) {
+  if (int rc = check_tiling(tl, msg)) return rc;
   pl.H = pr->H; pl.W = pr->W; pl.K = pr->K; pl.M = pr->M;
   pl.L = (2 * pl.M + 1) * (2 * pl.M + 1);
   pl.n = pl.H * pl.W;
@@ -153,6 +185,12 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
     if ((long long)nty * pl.ntx >= 304) { pl.THmax = th; break; }
   }
   if (!pl.THmax) pl.THmax = fallback ? fallback : H;
+  if (tl && tl->tile_rows) {
+    // requested height, raised until every tile of a multi-row tiling has >= 2M+1 rows
+    int th = tl->tile_rows;
+    while (th < H && (H + th - 1) / th > 1 && H / ((H + th - 1) / th) < 2 * M + 1) ++th;
+    pl.THmax = std::min(th, H);
+  }
   pl.nty = (H + pl.THmax - 1) / pl.THmax;
   pl.EHmax = pl.THmax + 2 * M + 1;
   pl.EWmax = pl.NC + 2 * M + 1;
@@ -178,8 +216,17 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   // larger ones: as many as fit (contiguous 64-byte pixel reads, fewer CTAs)
   const bool small_image = (long long)H * W < 65536;
   pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
+  if (tl && tl->row_pairs) {
+    const int qmax = row_pairs_per_cta(pl.Mf, Q);  // the most that fit a CTA
+    pl.QB = std::min(floor_pow2(tl->row_pairs), qmax);
+  }
   pl.nqblk = (Q + pl.QB - 1) / pl.QB;
-  pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB);
+  // row CTAs: 256 threads below a megapixel (several CTAs per SM hide the per-stage barrier
+  // latency), 1024 above (long rows, more work per CTA)
+  const bool large_image = (long long)H * W >= (1LL << 20);
+  pl.row_threads = large_image ? 1024 : 256;
+  if (tl && tl->row_threads) pl.row_threads = floor_pow2(tl->row_threads);
+  pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB, pl.row_threads);
   if (pl.row.smem > 227 * 1024) { msg = "row too long for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
   // column solve: column blocks of CB complex values, all H rows in shared memory (<= 64 KiB
   // so that several CTAs share an SM), NSEG segments per column
@@ -188,12 +235,17 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg) 
   if ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024) { msg = "image too tall for the column solve"; return SEGSALSA_ERR_ARG; }
   // small images: thinner column blocks so that the grid covers the GPU
   while (small_image && pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 8 * 152) pl.CB /= 2;
+  if (tl && tl->col_block) {
+    pl.CB = floor_pow2(tl->col_block);
+    while ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024 && pl.CB > 1) pl.CB /= 2;
+  }
   pl.col_smem = (size_t)H * pl.CB * sizeof(cplx<T>);
   const int nseq = 2 * pl.CB;
-  // segments of about 8 rows: the serial chain is two warm-ups plus two passes over a segment
-  // segment length: 8 rows for small images (short serial chains), 32 rows otherwise (the
-  // two warm-up recursions per segment then cost less than the segment itself)
-  pl.NSEG = std::max(1, std::min(H / (small_image ? 8 : 32), 1024 / nseq));
+  // segment length: 8 rows below a megapixel (short serial chains), 32 rows above (the two
+  // warm-up recursions per segment then cost less than the segment itself)
+  pl.col_rows = large_image ? 32 : 8;
+  if (tl && tl->col_rows) pl.col_rows = tl->col_rows;
+  pl.NSEG = std::max(1, std::min(H / pl.col_rows, 1024 / nseq));
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
   // diagnostics
@@ -320,9 +372,10 @@ class Solver : public SolverBase {
     if (own_stream && st) cudaStreamDestroy(st);
   }
 
-  int init(const segsalsa_str_params* pr, void* workspace, size_t wsbytes) {
+  int init(const segsalsa_str_params* pr, void* workspace, size_t wsbytes,
+           const segsalsa_str_tiling* tl = nullptr) {
     std::string msg;
-    int rc = make_plan<T>(pr, pl, msg);
+    int rc = make_plan<T>(pr, pl, msg, tl);
     if (rc) return fail(rc, msg);
     omega = make_weights(pr);
     lambda = pr->lambda;
@@ -796,6 +849,58 @@ class Solver : public SolverBase {
     for (int i = 0; i < NKIND; ++i) { nlaunch[i] = 0; ms[i] = 0; }
     return SEGSALSA_OK;
   }
+  segsalsa_str_tiling tiling() const override {
+    segsalsa_str_tiling t;
+    t.tile_rows = pl.THmax; t.row_pairs = pl.QB; t.col_block = pl.CB;
+    t.row_threads = pl.row_threads; t.col_rows = pl.col_rows;
+    return t;
+  }
+
+  // ------------------------------------------------------------------ batch support
+  bool ready() const override { return have_probs; }
+  bool graphable() const override { return have_probs && iter >= 1 && !rhs_dense; }
+  int enqueue_iterations(int len, cudaStream_t s) override {
+    cudaStream_t keep = st;
+    const bool keep_prof = profiling;
+    int64_t before[NKIND];
+    for (int i = 0; i < NKIND; ++i) before[i] = nlaunch[i];
+    st = s;
+    profiling = false;
+    int rc = SEGSALSA_OK;
+    for (int i = 0; i < len && !rc; ++i) {
+      rc = z_update(nullptr, b.z);
+      if (!rc) rc = sweep(false);
+    }
+    st = keep;
+    profiling = keep_prof;
+    for (int i = 0; i < NKIND; ++i) nlaunch[i] = before[i];
+    return rc;
+  }
+  void advance(int len) override {
+    iter += len;
+    nlaunch[KIND_ROWF] += len; nlaunch[KIND_COL] += len; nlaunch[KIND_ROWI] += len;
+    nlaunch[KIND_SWEEP] += len;
+  }
+  int enqueue_eager_iteration(cudaStream_t s) override {
+    cudaStream_t keep = st;
+    const bool keep_prof = profiling;
+    st = s;
+    profiling = false;
+    const int rc = iteration(false, 0);
+    st = keep;
+    profiling = keep_prof;
+    return rc;
+  }
+  int enqueue_read_err(int* host, cudaStream_t s) override {
+    SGS_CUDA(cudaMemcpyAsync(host, b.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return SEGSALSA_OK;
+  }
+  int clear_err(cudaStream_t s) override {
+    SGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), s));
+    return SEGSALSA_OK;
+  }
+  void invalidate() override { have_probs = false; iter = 0; rhs_dense = false; }
+
   int traffic(double* sw, double* it) const override {
     const double unit = (double)sizeof(T) * pl.n * pl.K;
     if (sw) *sw = unit * (4.0 * pl.L + 9.0);
@@ -805,17 +910,19 @@ class Solver : public SolverBase {
 };
 
 static int create_any(const segsalsa_str_params* pr, void* ws, size_t wsb,
-                      std::unique_ptr<SolverBase>& out, std::string& msg) {
+                      std::unique_ptr<SolverBase>& out, std::string& msg,
+                      const segsalsa_str_tiling* tl = nullptr) {
   int rc = check_params(pr, msg);
   if (rc) return rc;
+  if ((rc = check_tiling(tl, msg))) return rc;
   if (pr->precision == SEGSALSA_FP32) {
     auto s = std::make_unique<Solver<float>>();
-    rc = s->init(pr, ws, wsb);
+    rc = s->init(pr, ws, wsb, tl);
     if (rc) { msg = s->err; return rc; }
     out = std::move(s);
   } else {
     auto s = std::make_unique<Solver<double>>();
-    rc = s->init(pr, ws, wsb);
+    rc = s->init(pr, ws, wsb, tl);
     if (rc) { msg = s->err; return rc; }
     out = std::move(s);
   }
@@ -828,20 +935,439 @@ struct segsalsa_str {
   std::unique_ptr<sgs::SolverBase> impl;
 };
 
+// ------------------------------------------------------------------------------ batches
+//
+// A batch keeps one solver per image and a few "lanes" (streams). Images are assigned to lanes
+// by longest-processing-time-first on a per-iteration cost (bytes moved plus a fixed launch
+// term), so that the lanes carry about the same work. A chunk of `len` iterations of the whole
+// batch is captured once into a CUDA graph: the master stream forks to every lane, each lane
+// runs its images one after the other (all `len` iterations of an image in a row, so that a
+// small image's working set stays in L2), and the lanes join back. The chains of different
+// lanes run concurrently; replaying the graph costs one launch per chunk.
+namespace sgs {
+
+struct TuneKey {
+  int precision, M, K, size_class;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(precision, M, K, size_class) < std::tie(o.precision, o.M, o.K, o.size_class);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, segsalsa_str_tiling> g_tune_cache;
+static thread_local std::string g_batch_error;
+
+static int size_class_of(int H, int W) {
+  const long long n = (long long)H * W;
+  int l = 0;
+  while ((2LL << l) <= n) ++l;  // l = floor(log2 n)
+  return l / 2;
+}
+static TuneKey tune_key(const segsalsa_str_params& p) {
+  return TuneKey{p.precision, p.M, p.K, size_class_of(p.H, p.W)};
+}
+static bool same_tiling(const segsalsa_str_tiling& a, const segsalsa_str_tiling& b) {
+  return a.tile_rows == b.tile_rows && a.row_pairs == b.row_pairs && a.col_block == b.col_block &&
+         a.row_threads == b.row_threads && a.col_rows == b.col_rows;
+}
+
+constexpr int BATCH_CHUNK = 64;         // iterations per captured graph
+constexpr int BATCH_DEFAULT_LANES = 16;
+
+}  // namespace sgs
+
+struct segsalsa_str_batch {
+  std::string err;
+  int n = 0;
+  std::vector<segsalsa_str_params> params;
+  std::vector<std::vector<double>> weights;  // the callers' weights, copied
+  std::vector<std::unique_ptr<segsalsa_str>> img;
+  std::vector<segsalsa_str_tiling> req;      // requested tiling of each image (0 = default)
+  cudaStream_t ms = nullptr;
+  bool own_ms = false;
+  int nlanes = 0;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  std::vector<std::vector<int>> lane_img;
+  std::map<int, cudaGraphExec_t> graphs;     // by chunk length
+  int* err_host = nullptr;                   // pinned, one flag per image
+
+  int fail(int code, const std::string& m) { err = m; return code; }
+#define SGB_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(SEGSALSA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+  ~segsalsa_str_batch() {
+    if (ms) cudaStreamSynchronize(ms);
+    drop_graphs();
+    img.clear();
+    for (auto e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (auto s : lanes) cudaStreamDestroy(s);
+    if (err_host) cudaFreeHost(err_host);
+    if (own_ms && ms) cudaStreamDestroy(ms);
+  }
+
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+
+  // per-iteration cost used to balance the lanes: algorithmic bytes plus ~8 MB for the four
+  // launches' fixed latency
+  double cost(int i) const {
+    const auto& p = params[i];
+    const int L = (2 * p.M + 1) * (2 * p.M + 1);
+    const double es = p.precision == SEGSALSA_FP32 ? 4.0 : 8.0;
+    return es * (4.0 * L + 11.0) * (double)p.H * p.W * p.K + 8.0e6;
+  }
+
+  int make_image(int i, const segsalsa_str_tiling* t, std::unique_ptr<sgs::SolverBase>& out) {
+    std::string msg;
+    segsalsa_str_params pr = params[i];
+    pr.weights = weights[i].empty() ? nullptr : weights[i].data();
+    pr.stream = nullptr;
+    const int rc = sgs::create_any(&pr, nullptr, 0, out, msg, t);
+    if (rc) return fail(rc, "image " + std::to_string(i) + ": " + msg);
+    return SEGSALSA_OK;
+  }
+
+  int init(int count, const segsalsa_str_params* pr, const segsalsa_str_tiling* tl, void* stream) {
+    n = count;
+    params.assign(pr, pr + n);
+    weights.resize(n);
+    req.resize(n);
+    for (int i = 0; i < n; ++i) {
+      std::string msg;
+      if (int rc = sgs::check_params(&pr[i], msg)) return fail(rc, "image " + std::to_string(i) + ": " + msg);
+      if (pr[i].stream) return fail(SEGSALSA_ERR_ARG, "image " + std::to_string(i) + ": params.stream must be NULL in a batch");
+      if (tl)
+        if (int rc = sgs::check_tiling(&tl[i], msg)) return fail(rc, "image " + std::to_string(i) + ": " + msg);
+      const int L = (2 * pr[i].M + 1) * (2 * pr[i].M + 1);
+      if (pr[i].weights) weights[i].assign(pr[i].weights, pr[i].weights + L);
+      params[i].weights = nullptr;
+      if (tl) {
+        req[i] = tl[i];
+      } else {
+        std::lock_guard<std::mutex> g(sgs::g_tune_mu);
+        auto it = sgs::g_tune_cache.find(sgs::tune_key(pr[i]));
+        req[i] = it != sgs::g_tune_cache.end() ? it->second : segsalsa_str_tiling{0, 0, 0, 0, 0};
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      std::unique_ptr<sgs::SolverBase> s;
+      if (int rc = make_image(i, &req[i], s)) return rc;
+      img.emplace_back(new segsalsa_str);
+      img.back()->impl = std::move(s);
+    }
+    if (stream) ms = reinterpret_cast<cudaStream_t>(stream);
+    else { SGB_CUDA(cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking)); own_ms = true; }
+    SGB_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    SGB_CUDA(cudaMallocHost(&err_host, sizeof(int) * n));
+    return set_lanes(std::min(n, sgs::BATCH_DEFAULT_LANES));
+  }
+
+  // Longest-processing-time-first assignment of the images to `want` lanes.
+  int set_lanes(int want) {
+    if (want < 1) return fail(SEGSALSA_ERR_ARG, "lanes must be >= 1");
+    want = std::min(want, n);
+    while ((int)lanes.size() < want) {
+      cudaStream_t s;
+      SGB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      lanes.push_back(s);
+      cudaEvent_t e;
+      SGB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      join.push_back(e);
+    }
+    nlanes = want;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    lane_img.assign(nlanes, {});
+    std::vector<double> load(nlanes, 0.0);
+    for (int i : order) {
+      const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lane_img[j].push_back(i);
+      load[j] += cost(i);
+    }
+    drop_graphs();
+    return SEGSALSA_OK;
+  }
+
+  // Fork from the master stream to the lanes, run `body(lane, stream)`, join back.
+  template <class F> int on_lanes(F&& body) {
+    SGB_CUDA(cudaEventRecord(fork, ms));
+    int rc = SEGSALSA_OK;
+    for (int j = 0; j < nlanes; ++j) {
+      SGB_CUDA(cudaStreamWaitEvent(lanes[j], fork, 0));
+      if (!rc) rc = body(j, lanes[j]);
+      SGB_CUDA(cudaEventRecord(join[j], lanes[j]));
+      SGB_CUDA(cudaStreamWaitEvent(ms, join[j], 0));
+    }
+    return rc;
+  }
+
+  int image_fail(int i) {
+    return fail(SEGSALSA_ERR_CUDA, "image " + std::to_string(i) + ": " + img[i]->impl->err);
+  }
+
+  int get_graph(int len, cudaGraphExec_t& out) {
+    auto it = graphs.find(len);
+    if (it != graphs.end()) { out = it->second; return SEGSALSA_OK; }
+    SGB_CUDA(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
+    int bad = -1;
+    const int rc = on_lanes([&](int j, cudaStream_t s) {
+      for (int i : lane_img[j])
+        if (img[i]->impl->enqueue_iterations(len, s)) { bad = i; return SEGSALSA_ERR_CUDA; }
+      return SEGSALSA_OK;
+    });
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ms, &g);
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (bad >= 0) return image_fail(bad);
+      if (rc) return rc;
+      return fail(SEGSALSA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail(SEGSALSA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    graphs[len] = ex;
+    out = ex;
+    return SEGSALSA_OK;
+  }
+
+  int check_errs() {
+    for (int i = 0; i < n; ++i)
+      if (img[i]->impl->enqueue_read_err(err_host + i, ms)) return image_fail(i);
+    SGB_CUDA(cudaStreamSynchronize(ms));
+    int rc = SEGSALSA_OK;
+    for (int i = 0; i < n; ++i)
+      if (err_host[i]) {
+        img[i]->impl->clear_err(ms);
+        if (!rc) rc = fail(SEGSALSA_ERR_TIMEOUT, "image " + std::to_string(i) + ": a device-side wait gave up (bounded wait exceeded)");
+      }
+    cudaStreamSynchronize(ms);
+    return rc;
+  }
+
+  // Enqueue `iters` iterations of every image on the master stream (no synchronization).
+  int enqueue_solve(int iters) {
+    if (iters <= 0) return SEGSALSA_OK;
+    int left = iters;
+    bool eager = false;
+    for (int i = 0; i < n; ++i) eager = eager || !img[i]->impl->graphable();
+    if (eager) {
+      // one eager iteration of every image: afterwards all of them are at a plain iteration
+      int bad = -1;
+      const int rc = on_lanes([&](int j, cudaStream_t s) {
+        for (int i : lane_img[j])
+          if (img[i]->impl->enqueue_eager_iteration(s)) { bad = i; return SEGSALSA_ERR_CUDA; }
+        return SEGSALSA_OK;
+      });
+      if (bad >= 0) return image_fail(bad);
+      if (rc) return rc;
+      --left;
+    }
+    while (left > 0) {
+      const int len = std::min(left, sgs::BATCH_CHUNK);
+      cudaGraphExec_t g;
+      if (int rc = get_graph(len, g)) return rc;
+      SGB_CUDA(cudaGraphLaunch(g, ms));
+      for (int i = 0; i < n; ++i) img[i]->impl->advance(len);
+      left -= len;
+    }
+    return SEGSALSA_OK;
+  }
+
+  int solve(int iters) {
+    if (iters < 0) return fail(SEGSALSA_ERR_ARG, "iters must be >= 0");
+    for (int i = 0; i < n; ++i)
+      if (!img[i]->impl->ready()) return fail(SEGSALSA_ERR_STATE, "image " + std::to_string(i) + ": set_probs first");
+    if (int rc = enqueue_solve(iters)) return rc;
+    return check_errs();
+  }
+
+  // ------------------------------------------------------------------------ autotuner
+  // Deterministic strictly positive probabilities for the timing runs (the cost of an
+  // iteration does not depend on the values).
+  int synthetic_probs(int i) {
+    const auto& p = params[i];
+    const size_t nK = (size_t)p.H * p.W * p.K;
+    uint32_t x = 2463534242u + 977u * (uint32_t)i;
+    auto next = [&]() { x ^= x << 13; x ^= x >> 17; x ^= x << 5; return 0.05 + (x >> 8) * (1.0 / 16777216.0); };
+    int rc;
+    if (p.precision == SEGSALSA_FP32) {
+      std::vector<float> v(nK);
+      for (auto& e : v) e = (float)next();
+      rc = img[i]->impl->set_probs(v.data(), SEGSALSA_LAYOUT_HWK, 0);
+    } else {
+      std::vector<double> v(nK);
+      for (auto& e : v) e = next();
+      rc = img[i]->impl->set_probs(v.data(), SEGSALSA_LAYOUT_HWK, 0);
+    }
+    if (rc) return fail(rc, "image " + std::to_string(i) + ": " + img[i]->impl->err);
+    return SEGSALSA_OK;
+  }
+
+  int rebuild(int i, const segsalsa_str_tiling& t) {
+    std::unique_ptr<sgs::SolverBase> s;
+    if (int rc = make_image(i, &t, s)) return rc;
+    SGB_CUDA(cudaStreamSynchronize(ms));
+    img[i]->impl = std::move(s);
+    req[i] = t;
+    drop_graphs();
+    return synthetic_probs(i);
+  }
+
+  // Device time of `trial` batch iterations (best of two graph replays after a warm one).
+  int time_batch(int trial, double& ms_out) {
+    if (int rc = enqueue_solve(1)) return rc;  // brings every image to a plain iteration
+    cudaGraphExec_t g;
+    if (int rc = get_graph(trial, g)) return rc;
+    cudaEvent_t a, c;
+    SGB_CUDA(cudaEventCreate(&a));
+    SGB_CUDA(cudaEventCreate(&c));
+    double best = 1e300;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(a, ms);
+      if (e == cudaSuccess) e = cudaGraphLaunch(g, ms);
+      if (e == cudaSuccess) e = cudaEventRecord(c, ms);
+      if (e == cudaSuccess) e = cudaEventSynchronize(c);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, c);
+      if (e == cudaSuccess && r > 0) best = std::min(best, (double)t);
+      for (int i = 0; i < n; ++i) img[i]->impl->advance(trial);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(c);
+    if (e != cudaSuccess) return fail(SEGSALSA_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+    if (int rc = check_errs()) return rc;
+    ms_out = best;
+    return SEGSALSA_OK;
+  }
+
+  int autotune(int trial, segsalsa_str_tiling* chosen) {
+    if (trial < 1) return fail(SEGSALSA_ERR_ARG, "trial_iters must be >= 1");
+    for (int i = 0; i < n; ++i)
+      if (int rc = synthetic_probs(i)) return rc;
+    double best;
+    if (int rc = time_batch(trial, best)) return rc;
+    // lanes first
+    {
+      std::set<int> cand = {4, 8, 16, 32, n};
+      int keep = nlanes;
+      for (int L : cand) {
+        if (L > n || L == nlanes || L < 1) continue;
+        const int prev = nlanes;
+        if (int rc = set_lanes(L)) return rc;
+        double t;
+        if (int rc = time_batch(trial, t)) return rc;
+        if (t < best * 0.98) { best = t; keep = L; }
+        else if (int rc = set_lanes(prev)) return rc;
+      }
+      if (nlanes != keep)
+        if (int rc = set_lanes(keep)) return rc;
+    }
+    // then the tiling of each class, largest total work first
+    std::map<sgs::TuneKey, std::vector<int>> groups;
+    for (int i = 0; i < n; ++i) groups[sgs::tune_key(params[i])].push_back(i);
+    std::vector<std::pair<double, sgs::TuneKey>> order;
+    for (auto& kv : groups) {
+      double w = 0;
+      for (int i : kv.second) w += cost(i);
+      order.push_back({-w, kv.first});
+    }
+    std::sort(order.begin(), order.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    const int cand_rows[] = {4, 6, 8, 12, 16, 24, 32};
+    const int cand_pairs[] = {1, 2, 4, 8, 16};
+    const int cand_cols[] = {1, 2, 4, 8};
+    const int cand_rthr[] = {128, 256, 512, 1024};
+    const int cand_seg[] = {8, 16, 32};
+    for (auto& o : order) {
+      const std::vector<int>& mem = groups[o.second];
+      segsalsa_str_tiling cur = req[mem[0]];
+      // resolved tilings already timed for this class
+      std::set<std::vector<int>> seen;
+      auto resolved = [&](const segsalsa_str_tiling& t, std::vector<int>& key) {
+        key.clear();
+        for (int i : mem) {
+          segsalsa_str_params pr = params[i];
+          pr.weights = weights[i].empty() ? nullptr : weights[i].data();
+          sgs::Plan pl;
+          std::string msg;
+          const int rc = pr.precision == SEGSALSA_FP32 ? sgs::make_plan<float>(&pr, pl, msg, &t)
+                                                       : sgs::make_plan<double>(&pr, pl, msg, &t);
+          if (rc) return false;
+          key.push_back(pl.THmax); key.push_back(pl.QB); key.push_back(pl.CB);
+          key.push_back(pl.row.threads); key.push_back(pl.NSEG);
+        }
+        return true;
+      };
+      std::vector<int> key;
+      if (resolved(cur, key)) seen.insert(key);
+      for (int f = 0; f < 5; ++f) {
+        const int* cvs[5] = {cand_rows, cand_pairs, cand_cols, cand_rthr, cand_seg};
+        const int ncs[5] = {7, 5, 4, 4, 3};
+        const int* cv = cvs[f];
+        const int nc = ncs[f];
+        segsalsa_str_tiling keep = cur;
+        for (int c = 0; c < nc; ++c) {
+          segsalsa_str_tiling t = cur;
+          int* fld[5] = {&t.tile_rows, &t.row_pairs, &t.col_block, &t.row_threads, &t.col_rows};
+          *fld[f] = cv[c];
+          if (!resolved(t, key) || seen.count(key)) continue;
+          seen.insert(key);
+          bool ok = true;
+          for (int i : mem) {
+            const int rc = rebuild(i, t);
+            if (rc == SEGSALSA_ERR_ARG) { ok = false; break; }
+            if (rc) return rc;
+          }
+          double tm = 1e300;
+          if (ok)
+            if (int rc = time_batch(trial, tm)) return rc;
+          if (ok && tm < best * 0.98) { best = tm; keep = t; }
+        }
+        cur = keep;
+        for (int i : mem)
+          if (!sgs::same_tiling(req[i], cur))
+            if (int rc = rebuild(i, cur)) return rc;
+      }
+      std::lock_guard<std::mutex> g(sgs::g_tune_mu);
+      sgs::g_tune_cache[o.second] = cur;
+    }
+    for (int i = 0; i < n; ++i) {
+      img[i]->impl->invalidate();
+      if (chosen) chosen[i] = img[i]->impl->tiling();
+    }
+    drop_graphs();
+    SGB_CUDA(cudaStreamSynchronize(ms));
+    return SEGSALSA_OK;
+  }
+#undef SGB_CUDA
+};
+
 extern "C" {
 
-int segsalsa_str_workspace_bytes(const segsalsa_str_params* pr, size_t* bytes) {
+int segsalsa_str_workspace_bytes_tiled(const segsalsa_str_params* pr, const segsalsa_str_tiling* tl,
+                                       size_t* bytes) {
   std::string msg;
   int rc = sgs::check_params(pr, msg);
   if (!rc && !bytes) { rc = SEGSALSA_ERR_ARG; msg = "bytes is NULL"; }
   if (!rc) {
     sgs::Plan pl;
     if (pr->precision == SEGSALSA_FP32) {
-      rc = sgs::make_plan<float>(pr, pl, msg);
+      rc = sgs::make_plan<float>(pr, pl, msg, tl);
       sgs::Buffers<float> b{};
       if (!rc) *bytes = sgs::carve<float>(pl, nullptr, b);
     } else {
-      rc = sgs::make_plan<double>(pr, pl, msg);
+      rc = sgs::make_plan<double>(pr, pl, msg, tl);
       sgs::Buffers<double> b{};
       if (!rc) *bytes = sgs::carve<double>(pl, nullptr, b);
     }
@@ -850,16 +1376,31 @@ int segsalsa_str_workspace_bytes(const segsalsa_str_params* pr, size_t* bytes) {
   return rc;
 }
 
-int segsalsa_str_create(const segsalsa_str_params* pr, void* ws, size_t wsb, segsalsa_str_t** out) {
+int segsalsa_str_workspace_bytes(const segsalsa_str_params* pr, size_t* bytes) {
+  return segsalsa_str_workspace_bytes_tiled(pr, nullptr, bytes);
+}
+
+int segsalsa_str_create_tiled(const segsalsa_str_params* pr, const segsalsa_str_tiling* tl, void* ws,
+                              size_t wsb, segsalsa_str_t** out) {
   if (!out) { sgs::g_last_error = "out is NULL"; return SEGSALSA_ERR_ARG; }
   *out = nullptr;
   std::unique_ptr<sgs::SolverBase> impl;
   std::string msg;
-  int rc = sgs::create_any(pr, ws, wsb, impl, msg);
+  int rc = sgs::create_any(pr, ws, wsb, impl, msg, tl);
   if (rc) { sgs::g_last_error = msg; return rc; }
   auto* h = new segsalsa_str;
   h->impl = std::move(impl);
   *out = h;
+  return SEGSALSA_OK;
+}
+
+int segsalsa_str_create(const segsalsa_str_params* pr, void* ws, size_t wsb, segsalsa_str_t** out) {
+  return segsalsa_str_create_tiled(pr, nullptr, ws, wsb, out);
+}
+
+int segsalsa_str_get_tiling(const segsalsa_str_t* h, segsalsa_str_tiling* t) {
+  if (!h || !t) return SEGSALSA_ERR_ARG;
+  *t = h->impl->tiling();
   return SEGSALSA_OK;
 }
 
@@ -904,6 +1445,47 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sw, double* it) 
   SGS_H(h); return h->impl->traffic(sw, it);
 }
 void segsalsa_str_destroy(segsalsa_str_t* h) { delete h; }
+
+int segsalsa_str_batch_create(int32_t n, const segsalsa_str_params* params,
+                              const segsalsa_str_tiling* tiling, void* stream,
+                              segsalsa_str_batch_t** out) {
+  if (!out) { sgs::g_batch_error = "out is NULL"; return SEGSALSA_ERR_ARG; }
+  *out = nullptr;
+  if (n < 1 || !params) { sgs::g_batch_error = "n_images must be >= 1 and params non-NULL"; return SEGSALSA_ERR_ARG; }
+  auto b = std::make_unique<segsalsa_str_batch>();
+  const int rc = b->init(n, params, tiling, stream);
+  if (rc) { sgs::g_batch_error = b->err; return rc; }
+  *out = b.release();
+  return SEGSALSA_OK;
+}
+int segsalsa_str_batch_image(segsalsa_str_batch_t* b, int32_t i, segsalsa_str_t** h) {
+  if (!b) return SEGSALSA_ERR_ARG;
+  if (!h || i < 0 || i >= b->n) return b->fail(SEGSALSA_ERR_ARG, "image index out of range or h NULL");
+  *h = b->img[i].get();
+  return SEGSALSA_OK;
+}
+int segsalsa_str_batch_solve(segsalsa_str_batch_t* b, int32_t iters) {
+  if (!b) return SEGSALSA_ERR_ARG;
+  return b->solve(iters);
+}
+int segsalsa_str_batch_autotune(segsalsa_str_batch_t* b, int32_t trial_iters, segsalsa_str_tiling* chosen) {
+  if (!b) return SEGSALSA_ERR_ARG;
+  return b->autotune(trial_iters, chosen);
+}
+int segsalsa_str_batch_set_lanes(segsalsa_str_batch_t* b, int32_t lanes) {
+  if (!b) return SEGSALSA_ERR_ARG;
+  return b->set_lanes(lanes);
+}
+int segsalsa_str_batch_get_lanes(const segsalsa_str_batch_t* b, int32_t* lanes) {
+  if (!b || !lanes) return SEGSALSA_ERR_ARG;
+  *lanes = b->nlanes;
+  return SEGSALSA_OK;
+}
+void segsalsa_str_batch_destroy(segsalsa_str_batch_t* b) { delete b; }
+const char* segsalsa_str_batch_last_error(const segsalsa_str_batch_t* b) {
+  if (!b) return sgs::g_batch_error.c_str();
+  return b->err.c_str();
+}
 const char* segsalsa_str_last_error(const segsalsa_str_t* h) {
   if (!h) return sgs::g_last_error.c_str();
   return h->impl->err.c_str();

@@ -74,3 +74,33 @@ def test_weights_validation(lib):
     w[3] = np.nan
     with pytest.raises(B.SegsalsaError):
         B.segsalsa_str_workspace_bytes(B.make_params(16, 16, 4, weights=w))
+
+
+def test_tiling_struct_matches_header():
+    assert ctypes.sizeof(B.Tiling) == 20
+    assert B.Tiling.row_pairs.offset == 4 and B.Tiling.col_rows.offset == 16
+
+
+@pytest.mark.parametrize("tiling,ok", [
+    ((0, 0, 0), True), ((4, 1, 1), True), ((32, 16, 8), True), ((3, 0, 0), False),
+    ((33, 0, 0), False), ((8, -1, 0), False), ((8, 0, 9), False), ((8, 65, 0), False),
+    ((0, 0, 0, 256, 16), True), ((0, 0, 0, 32, 0), False), ((0, 0, 0, 2048, 0), False),
+    ((0, 0, 0, 0, 1), False)])
+def test_tiling_checks(lib, tiling, ok):
+    pr = B.make_params(145, 145, 16)
+    t = B.make_tiling(*tiling)
+    if ok:
+        assert B.segsalsa_str_workspace_bytes_tiled(pr, t) > 0
+    else:
+        with pytest.raises(B.SegsalsaError) as e:
+            B.segsalsa_str_workspace_bytes_tiled(pr, t)
+        assert e.value.code == B.SEGSALSA_ERR_ARG
+
+
+def test_taller_tiles_need_fewer_partials(lib):
+    """The rhs tile partials hold every tile plus its halo rows: taller tiles, fewer halo rows,
+    a smaller workspace; no tiling equals the defaults."""
+    pr = B.make_params(512, 512, 16)
+    sizes = [B.segsalsa_str_workspace_bytes_tiled(pr, B.make_tiling(th)) for th in (4, 8, 16, 32)]
+    assert sizes == sorted(sizes, reverse=True) and sizes[0] > sizes[-1]
+    assert B.segsalsa_str_workspace_bytes_tiled(pr, None) == B.segsalsa_str_workspace_bytes(pr)

@@ -223,6 +223,7 @@ def test_device_pointers_and_scale_invariance(B):
     sc = synth.scene(32, 30, 8, S=5, gap=2.0, noise_std=1.0, wrong_frac=0.0, seed=34)
     s = _solver(B, 32, 30, 8, 1, 0.5, 1.5, 1.0, 1, "fp32")
     pt = torch.from_numpy(khw_to_hwk(sc.p.astype(np.float32))).cuda()
+    torch.cuda.synchronize()       # the handle's stream does not wait for torch's stream
     s.set_probs(pt, layout=1)
     s.solve(20)
     zd = torch.empty((8, 32, 30), dtype=torch.float32, device="cuda")
