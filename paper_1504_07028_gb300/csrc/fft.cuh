@@ -19,12 +19,19 @@
 // Spectrum layout: S[y][kx][k] complex, kx in [0, W/2].
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sgs {
 
 constexpr int FFT_MAXST = 24;
-constexpr int FFT_MAXE = 16;  // most complex values a thread holds per stage (largest variant)
+
+// Shared-memory slot of complex element i of a transform buffer: one pad slot after every 8
+// elements. The Stockham stages write with power-of-two strides (radix x sequences); without
+// the pad those writes fall on a few banks, with it they spread over all of them.
+__host__ __device__ __forceinline__ int px(int i) { return i + (i >> 3); }
+__host__ __device__ inline size_t padded_elems(size_t n) { return n + (n >> 3) + 1; }
 
 template <typename T>
 struct FftPlan {
@@ -128,99 +135,88 @@ __device__ __forceinline__ int qdiv(int t, uint32_t mg) {
 }
 
 // One forward Stockham stage of radix R in {2,3,4,5,7,8} on B = 2^lgB interleaved sequences
-// X[n * B + b]: each work item is one radix-R butterfly (in place: every thread reads its
-// inputs, the block synchronises, then writes).
-template <typename T, int R, int MAXE>
-__device__ __forceinline__ void fft_stage(cplx<T>* X, int B, uint32_t mgB, int Mf, int Ns,
-                                          uint32_t mg, const cplx<T>* tw, int S) {
+// X[n * B + b], out of place: each work item is one radix-R butterfly reading Xin and writing
+// Xout; the caller synchronises the block between stages.
+template <typename T, int R>
+__device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ Xin, cplx<T>* __restrict__ Xout,
+                                          int B, uint32_t mgB, int Mf, int Ns, uint32_t mg,
+                                          const cplx<T>* tw, int S) {
   using C = cplx<T>;
-  constexpr int MI = (MAXE + R - 1) / R;
   const int nb = Mf / R;
   const int items = nb * B;
   const int stride = nb / Ns;
-  C out[MI][R];
-  int base[MI];
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int t = qdiv(it, mgB), b = it - t * B;
+    const int g = qdiv(t, mg);
+    const int j = t - g * Ns;
+    C v[R];
 #pragma unroll
-  for (int q = 0; q < MI; ++q) {
-    const int it = threadIdx.x + q * blockDim.x;
-    base[q] = -1;
-    if (it < items) {
-      const int t = qdiv(it, mgB), b = it - t * B;
-      const int g = qdiv(t, mg);
-      const int j = t - g * Ns;
-      C v[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = X[(t + r * nb) * S + b];
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * j * stride]);
-      Dft<R, C>::run(v);
-#pragma unroll
-      for (int r = 0; r < R; ++r) out[q][r] = v[r];
-      base[q] = (g * Ns * R + j) * S + b;
+    for (int r = 0; r < R; ++r) v[r] = Xin[px((t + r * nb) * S + b)];
+    // twiddles w^r, w = tw[j * stride]: w and (for R > 5) w^4 from the table, the other
+    // powers by at most two products
+    {
+      const C w1 = tw[j * stride];
+      v[1] = cmul(v[1], w1);
+      if (R > 2) {
+        const C w2 = cmul(w1, w1);
+        v[2] = cmul(v[2], w2);
+        if (R > 3) {
+          const C w3 = cmul(w2, w1);
+          v[3] = cmul(v[3], w3);
+          if (R > 4) {
+            const C w4 = (R > 5) ? tw[4 * j * stride] : cmul(w2, w2);
+            v[4] = cmul(v[4], w4);
+            if (R > 5) {
+              v[5] = cmul(v[5], cmul(w4, w1));
+              v[6] = cmul(v[6], cmul(w4, w2));
+            }
+            if (R > 7) v[7] = cmul(v[7], cmul(w4, w3));
+          }
+        }
+      }
     }
-  }
-  __syncthreads();
+    Dft<R, C>::run(v);
+    const int base = (g * Ns * R + j) * S + b;
 #pragma unroll
-  for (int q = 0; q < MI; ++q) {
-    if (base[q] >= 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) X[base[q] + r * Ns * S] = out[q][r];
-    }
+    for (int r = 0; r < R; ++r) Xout[px(base + r * Ns * S)] = v[r];
   }
-  __syncthreads();
 }
 
 // A Stockham stage of prime radix R > 7 computed output by output: output o of sequence b is
 // sum_r X[t + r nb] w^{r (j s + m nb)} with o = g Ns R + m Ns + j, t = g Ns + j, s = nb / Ns
-// (twiddle and the radix-R DFT root folded into one table index). MAXE outputs per thread.
-template <typename T, int MAXE>
-__device__ __forceinline__ void fft_direct_stage(cplx<T>* X, int B, uint32_t mgB, int Mf, int R,
-                                                 int Ns, uint32_t mg_ns, uint32_t mg_nsr,
-                                                 const cplx<T>* tw, int S) {
+// (twiddle and the radix-R DFT root folded into one table index). Out of place.
+template <typename T>
+__device__ __forceinline__ void fft_direct_stage(const cplx<T>* __restrict__ Xin,
+                                                 cplx<T>* __restrict__ Xout, int B, uint32_t mgB,
+                                                 int Mf, int R, int Ns, uint32_t mg_ns,
+                                                 uint32_t mg_nsr, const cplx<T>* tw, int S) {
   using C = cplx<T>;
   const int nb = Mf / R;
   const int items = Mf * B;
   const int s = nb / Ns;
   const int NsR = Ns * R;
-  C out[MAXE];
-#pragma unroll
-  for (int q = 0; q < MAXE; ++q) {
-    const int it = threadIdx.x + q * blockDim.x;
-    out[q] = mkc<T>(T(0), T(0));
-    if (it < items) {
-      const int o = qdiv(it, mgB), b = it - o * B;
-      const int g = qdiv(o, mg_nsr);
-      const int rem = o - g * NsR;
-      const int m = qdiv(rem, mg_ns);
-      const int j = rem - m * Ns;
-      const int t = g * Ns + j;
-      int step = j * s + m * nb;
-      step -= (step >= Mf) ? Mf : 0;
-      int idx = 0;
-      T ax = T(0), ay = T(0);
-      const C* src = X + t * S + b;
-      for (int r = 0; r < R; ++r) {
-        const C v = src[r * nb * S];
-        const C w = tw[idx];
-        ax += v.x * w.x - v.y * w.y;
-        ay += v.x * w.y + v.y * w.x;
-        idx += step;
-        idx -= (idx >= Mf) ? Mf : 0;
-      }
-      out[q].x = ax;
-      out[q].y = ay;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int o = qdiv(it, mgB), b = it - o * B;
+    const int g = qdiv(o, mg_nsr);
+    const int rem = o - g * NsR;
+    const int m = qdiv(rem, mg_ns);
+    const int j = rem - m * Ns;
+    const int t = g * Ns + j;
+    int step = j * s + m * nb;
+    step -= (step >= Mf) ? Mf : 0;
+    int idx = 0;
+    T ax = T(0), ay = T(0);
+    const int src = t * S + b;
+    for (int r = 0; r < R; ++r) {
+      const C v = Xin[px(src + r * nb * S)];
+      const C w = tw[idx];
+      ax += v.x * w.x - v.y * w.y;
+      ay += v.x * w.y + v.y * w.x;
+      idx += step;
+      idx -= (idx >= Mf) ? Mf : 0;
     }
+    Xout[px(o * S + b)] = mkc<T>(ax, ay);
   }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < MAXE; ++q) {
-    const int it = threadIdx.x + q * blockDim.x;
-    if (it < items) {
-      const int o = qdiv(it, mgB), b = it - o * B;
-      X[o * S + b] = out[q];
-    }
-  }
-  __syncthreads();
 }
 
 // Shared-memory copies of the transform tables, filled at kernel start.
@@ -231,25 +227,33 @@ struct FftTables {
   const cplx<T>* bhat;
 };
 
-template <typename T, int MAXE>
-__device__ void fft_forward(cplx<T>* X, int B, uint32_t mgB, const FftPlan<T>& pl,
-                            const cplx<T>* tw, int S = -1) {
+// All stages of the plan, ping-ponging between X (holding the input; the caller has
+// synchronised after filling it) and Y. Returns the buffer that holds the result; the block
+// is synchronised on return.
+template <typename T>
+__device__ cplx<T>* fft_forward(cplx<T>* X, cplx<T>* Y, int B, uint32_t mgB, const FftPlan<T>& pl,
+                                const cplx<T>* tw, int S = -1) {
   if (S < 0) S = B;  // element stride (sequences [0, B) interleaved at unit stride)
+  cplx<T>* in = X;
+  cplx<T>* out = Y;
   for (int s = 0; s < pl.nst; ++s) {
     const int Ns = pl.ns[s];
     const uint32_t mg = pl.mg_ns[s];
     switch (pl.radix[s]) {
-      case 8: fft_stage<T, 8, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
-      case 4: fft_stage<T, 4, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
-      case 2: fft_stage<T, 2, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
-      case 3: fft_stage<T, 3, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
-      case 5: fft_stage<T, 5, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
-      case 7: fft_stage<T, 7, MAXE>(X, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 8: fft_stage<T, 8>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 4: fft_stage<T, 4>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 2: fft_stage<T, 2>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 3: fft_stage<T, 3>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 5: fft_stage<T, 5>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
+      case 7: fft_stage<T, 7>(in, out, B, mgB, pl.Mf, Ns, mg, tw, S); break;
       default:
-        fft_direct_stage<T, MAXE>(X, B, mgB, pl.Mf, pl.radix[s], Ns, mg, pl.mg_nsr[s], tw, S);
+        fft_direct_stage<T>(in, out, B, mgB, pl.Mf, pl.radix[s], Ns, mg, pl.mg_nsr[s], tw, S);
         break;
     }
+    __syncthreads();
+    cplx<T>* t = in; in = out; out = t;
   }
+  return in;
 }
 
 // Bytes of shared memory for the tables of a plan (twiddles, and for Bluestein the chirp and
@@ -277,33 +281,31 @@ __device__ inline FftTables<T> load_tables(const FftPlan<T>& pl, cplx<T>* tab) {
 }
 
 // Forward DFT of length N of the B sequences in X (slots [0, N) filled, Bluestein slots
-// [N, Mf) need not be). Afterwards X[k*B + b], k < N, holds X_k for the mixed-radix path; for
-// Bluestein the caller reads bluestein_out(k).
-template <typename T, int MAXE>
-__device__ void dft_rows(cplx<T>* X, int B, uint32_t mgB, const FftPlan<T>& pl,
-                         const FftTables<T>& tb) {
-  if (!pl.blue) {
-    fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);
-    return;
-  }
-  // a_n = x_n conj(chirp_n), zero padded
+// [N, Mf) need not be; the caller has synchronised). Y is the second buffer of the same
+// size. Returns the buffer R with R[k*B + b], k < N, holding X_k for the mixed-radix path;
+// for Bluestein the caller reads dft_out(R, k).
+template <typename T>
+__device__ cplx<T>* dft_rows(cplx<T>* X, cplx<T>* Y, int B, uint32_t mgB, const FftPlan<T>& pl,
+                             const FftTables<T>& tb) {
+  if (!pl.blue) return fft_forward<T>(X, Y, B, mgB, pl, tb.tw);
+  // a_n = x_n conj(chirp_n), zero padded (each thread rewrites only its own elements)
   for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x) {
     const int n = qdiv(i, mgB);
-    X[i] = (n < pl.N) ? cmulc(X[i], tb.chirp[n]) : mkc<T>(T(0), T(0));
+    X[px(i)] = (n < pl.N) ? cmulc(X[px(i)], tb.chirp[n]) : mkc<T>(T(0), T(0));
   }
   __syncthreads();
-  fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);
+  cplx<T>* A = fft_forward<T>(X, Y, B, mgB, pl, tb.tw);
   for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x)
-    X[i] = cconj(cmul(X[i], tb.bhat[qdiv(i, mgB)]));
+    A[px(i)] = cconj(cmul(A[px(i)], tb.bhat[qdiv(i, mgB)]));
   __syncthreads();
-  fft_forward<T, MAXE>(X, B, mgB, pl, tb.tw);  // = conj(cyclic convolution)
+  return fft_forward<T>(A, A == X ? Y : X, B, mgB, pl, tb.tw);  // = conj(cyclic convolution)
 }
 
-// Value X_k after dft_rows.
+// Value X_k of sequence b after dft_rows (R is the buffer it returned).
 template <typename T>
-__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* X, int B, int k, int b,
+__device__ __forceinline__ cplx<T> dft_out(const cplx<T>* R, int B, int k, int b,
                                            const FftPlan<T>& pl, const FftTables<T>& tb) {
-  const cplx<T> v = X[k * B + b];
+  const cplx<T> v = R[px(k * B + b)];
   if (!pl.blue) return v;
   return cconj(cmul(tb.chirp[k], v));  // conj(chirp_k) * (a * b)_k
 }
@@ -353,18 +355,23 @@ __device__ __forceinline__ T gather_rhs(const RowArgs<T>& a, int y, int x, int k
 
 // Same sum for a row whose two vertical covers start at P offsets rb0 / rb1 (-1 when absent),
 // with the per-column offsets offX in shared memory. Same summation order as gather_rhs.
+// Every row has a first vertical cover (rb0 >= 0) and every column a first horizontal one
+// (o0 >= 0). The four loads are unconditional (an absent cover aliases the first one, whose
+// value is then dropped by a select), so that the loads of all the elements a thread gathers
+// can be in flight together.
 template <typename T>
-__device__ __forceinline__ T gather_row(const T* P, int rb0, int rb1, const int* oX, int x, int k) {
-  T v = T(0);
-  const int o0 = oX[2 * x], o1 = oX[2 * x + 1];
-  if (rb0 >= 0) {
-    if (o0 >= 0) v += P[rb0 + o0 + k];
-    if (o1 >= 0) v += P[rb0 + o1 + k];
-  }
-  if (rb1 >= 0) {
-    if (o0 >= 0) v += P[rb1 + o0 + k];
-    if (o1 >= 0) v += P[rb1 + o1 + k];
-  }
+__device__ __forceinline__ T gather_row(const T* __restrict__ P, int rb0, int rb1, const int* oX,
+                                        int x, int k) {
+  const int o0 = oX[2 * x], o1r = oX[2 * x + 1];
+  const bool hx = o1r >= 0, hy = rb1 >= 0;
+  const int o1 = hx ? o1r : o0;
+  const int r1 = hy ? rb1 : rb0;
+  const T p00 = __ldg(P + rb0 + o0 + k), p01 = __ldg(P + rb0 + o1 + k);
+  const T p10 = __ldg(P + r1 + o0 + k), p11 = __ldg(P + r1 + o1 + k);
+  T v = p00;
+  v += hx ? p01 : T(0);
+  v += hy ? p10 : T(0);
+  v += (hx && hy) ? p11 : T(0);
   return v;
 }
 
@@ -385,8 +392,8 @@ __device__ __forceinline__ uint32_t div_magic_dev(int d) {
 // Shared memory of a row-pass CTA: transform buffer, tables, horizontal offset table.
 template <typename T>
 __host__ __device__ inline size_t row_smem_bytes(int N, int Mf, int blue, int QB, int tables) {
-  return sizeof(cplx<T>) * (size_t)Mf * QB + (tables ? fft_table_bytes<T>(N, Mf, blue) : 0) +
-         sizeof(int) * 2 * (size_t)N;
+  return sizeof(cplx<T>) * 2 * padded_elems((size_t)Mf * QB) +
+         (tables ? fft_table_bytes<T>(N, Mf, blue) : 0) + sizeof(int) * 2 * (size_t)N;
 }
 template <typename T>
 __device__ inline FftTables<T> row_tables(const RowArgs<T>& a, cplx<T>* tab) {
@@ -394,17 +401,20 @@ __device__ inline FftTables<T> row_tables(const RowArgs<T>& a, cplx<T>* tab) {
   return FftTables<T>{a.pl.tw, a.pl.chirp, a.pl.bhat};
 }
 
-template <typename T, int MAXE>
+template <typename T>
 __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   using C = cplx<T>;
-  constexpr int U = 4;  // independent element loads in flight per thread
+  constexpr int U = 8;  // independent element loads in flight per thread
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  const int y = blockIdx.x;
-  const int q0 = blockIdx.y * a.QB;
+  // grid (class blocks, rows): the class blocks of one row run side by side, so the 32-byte
+  // sectors they share are read from DRAM once
+  const int y = blockIdx.y;
+  const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
-  C* tab = X + (size_t)a.pl.Mf * B;
+  C* Y = X + padded_elems((size_t)a.pl.Mf * B);  // second transform buffer
+  C* tab = Y + padded_elems((size_t)a.pl.Mf * B);
   int* cX = reinterpret_cast<int*>(
       tab + (a.smem_tables ? fft_table_bytes<T>(N, a.pl.Mf, a.pl.blue) / sizeof(C) : 0));
   const FftTables<T> tb = row_tables<T>(a, tab);
@@ -437,11 +447,11 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
-      if (i < tot) Xf[i] = v[u];
+      if (i < tot) Xf[2 * px(i >> 1) + (i & 1)] = v[u];
     }
   }
   __syncthreads();
-  dft_rows<T, MAXE>(X, B, a.mgB, a.pl, tb);
+  const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
   pdl_trigger();
   // unpack the two real spectra: A = (X_k + conj X_{N-k})/2, B = (X_k - conj X_{N-k})/(2i)
   for (int i = threadIdx.x; i < a.Wh * B * 2; i += blockDim.x) {
@@ -450,8 +460,8 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
     const int kx = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C u = dft_out<T>(X, B, kx, qq, a.pl, tb);
-    const C w = dft_out<T>(X, B, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
+    const C u = dft_out<T>(R, B, kx, qq, a.pl, tb);
+    const C w = dft_out<T>(R, B, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
     C o;
     if (part == 0) { o.x = T(0.5) * (u.x + w.x); o.y = T(0.5) * (u.y - w.y); }
     else           { o.x = T(0.5) * (u.y + w.y); o.y = T(0.5) * (w.x - u.x); }
@@ -470,17 +480,20 @@ __global__ void k_gather_dense(const RowArgs<T> a) {
 }
 
 // ------------------------------------------------------------------- pass C (inverse rows)
-template <typename T, int MAXE>
+template <typename T>
 __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   using C = cplx<T>;
-  constexpr int U = 4;
+  constexpr int U = 8;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  const int y = blockIdx.x;
-  const int q0 = blockIdx.y * a.QB;
+  // grid (class blocks, rows): the class blocks of one row run side by side, so the 32-byte
+  // sectors they share are read from DRAM once
+  const int y = blockIdx.y;
+  const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
-  C* tab = X + (size_t)a.pl.Mf * B;
+  C* Y = X + padded_elems((size_t)a.pl.Mf * B);  // second transform buffer
+  C* tab = Y + padded_elems((size_t)a.pl.Mf * B);
   const FftTables<T> tb = row_tables<T>(a, tab);
   cp_async_commit();
   pdl_wait();  // the spectrum comes from the column pass
@@ -511,13 +524,13 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
         C A = Av[u], Bq = Bv[u];
         if ((i >> a.lgB) >= a.Wh) { A = cconj(A); Bq = cconj(Bq); }
         C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);   // conj(A + i B)
-        X[i] = xv;
+        X[px(i)] = xv;
       }
     }
   }
   cp_async_wait_all();
   __syncthreads();
-  dft_rows<T, MAXE>(X, B, a.mgB, a.pl, tb);
+  const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
   pdl_trigger();
   const T inv = T(1) / T(N);
   for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
@@ -526,7 +539,7 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
     const int x = (i >> 1) >> a.lgB;
     const int k = 2 * (q0 + qq) + part;
     if (k >= a.K) continue;
-    const C v = dft_out<T>(X, B, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
+    const C v = dft_out<T>(R, B, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
     a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
   }
 }
@@ -617,18 +630,18 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
 
 // ---------------------------------------------------------------- host-side launch helpers
 struct RowLaunch {
-  int maxe;       // complex values per thread per stage (4, 8 or 16)
   int threads;
   int tables;     // tables in shared memory
   size_t smem;
 };
 
-// Class pairs per CTA for a row transform of length Mf: a power of two, at most 8192 complex
-// values a CTA; halved (down to 128 values a CTA) while the grid has fewer than eight CTAs per
-// SM, so that small images spread over the GPU instead of running long per-CTA chains.
-inline int row_pairs_per_cta(int Mf, int Q, int rows = 1 << 30) {
+// Class pairs per CTA for a row transform of length Mf: a power of two, at most `max_elems`
+// complex values a CTA (each of its two transform buffers); halved (down to 128 values a CTA)
+// while the grid has fewer than eight CTAs per SM, so that small images spread over the GPU
+// instead of running long per-CTA chains.
+inline int row_pairs_per_cta(int Mf, int Q, int rows = 1 << 30, int max_elems = 4096) {
   int qb = 1;
-  while (qb < Q && 2 * qb * Mf <= 8192) qb *= 2;
+  while (qb < Q && 2 * qb * Mf <= max_elems) qb *= 2;
   while (qb > 1 && (long long)rows * ((Q + qb - 1) / qb) < 8 * 152 && Mf * qb / 2 >= 128) qb /= 2;
   return qb;
 }
@@ -688,12 +701,11 @@ inline bool make_fft_plan(int N, FftPlan<T>& pl) {
 template <typename T>
 inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_threads = 1024) {
   RowLaunch r{};
+  // one radix-8 butterfly (eight values) per thread and stage; fewer threads loop
   const int elems = Mf * QB;
-  r.maxe = 1;
-  while (r.maxe < 16 && (elems + r.maxe - 1) / r.maxe > target_threads) r.maxe *= 2;
-  int t = (elems + r.maxe - 1) / r.maxe;
-  t = (t + 31) / 32 * 32;
-  r.threads = t < 64 ? 64 : (t > 1024 ? 1024 : t);
+  int t = (elems / 8 + 31) / 32 * 32;
+  const int cap = std::min(target_threads, 1024);
+  r.threads = t < 64 ? 64 : (t > cap ? cap : t);
   r.tables = row_smem_bytes<T>(N, Mf, blue, QB, 1) <= 160 * 1024;
   r.smem = row_smem_bytes<T>(N, Mf, blue, QB, r.tables);
   return r;
@@ -720,65 +732,36 @@ cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem);
 
 
 #ifdef SGS_FFT_INSTANTIATE
-template <typename T, int MAXE>
+template <typename T>
 struct RowGrant {
   static size_t f, i;
 };
-template <typename T, int MAXE> size_t RowGrant<T, MAXE>::f = 0;
-template <typename T, int MAXE> size_t RowGrant<T, MAXE>::i = 0;
+template <typename T> size_t RowGrant<T>::f = 0;
+template <typename T> size_t RowGrant<T>::i = 0;
 template <typename T>
 struct ColGrant {
   static size_t g;
 };
 template <typename T> size_t ColGrant<T>::g = 0;
 
-template <typename T, int MAXE>
-inline cudaError_t prepare_row_inst(size_t smem) {
-  cudaError_t e = grant_smem(k_row_forward<T, MAXE>, smem, RowGrant<T, MAXE>::f);
-  if (e != cudaSuccess) return e;
-  return grant_smem(k_row_inverse<T, MAXE>, smem, RowGrant<T, MAXE>::i);
-}
-
 template <typename T>
 cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem) {
-  cudaError_t e;
-  switch (rl.maxe) {
-    case 1: e = prepare_row_inst<T, 1>(rl.smem); break;
-    case 2: e = prepare_row_inst<T, 2>(rl.smem); break;
-    case 4: e = prepare_row_inst<T, 4>(rl.smem); break;
-    case 8: e = prepare_row_inst<T, 8>(rl.smem); break;
-    default: e = prepare_row_inst<T, 16>(rl.smem); break;
-  }
+  cudaError_t e = grant_smem(k_row_forward<T>, rl.smem, RowGrant<T>::f);
   if (e != cudaSuccess) return e;
+  if ((e = grant_smem(k_row_inverse<T>, rl.smem, RowGrant<T>::i)) != cudaSuccess) return e;
   return grant_smem(k_col_solve<T>, col_smem, ColGrant<T>::g);
-}
-
-template <typename T, int MAXE>
-inline cudaError_t launch_row_inst(bool forward, const RowArgs<T>& a, dim3 grid,
-                                   const RowLaunch& rl, cudaStream_t st) {
-  size_t& gf = RowGrant<T, MAXE>::f;
-  size_t& gi = RowGrant<T, MAXE>::i;
-  cudaError_t e;
-  if (forward) {
-    if ((e = grant_smem(k_row_forward<T, MAXE>, rl.smem, gf)) != cudaSuccess) return e;
-    e = launch_pdl(k_row_forward<T, MAXE>, grid, dim3(rl.threads), rl.smem, st, a);
-  } else {
-    if ((e = grant_smem(k_row_inverse<T, MAXE>, rl.smem, gi)) != cudaSuccess) return e;
-    e = launch_pdl(k_row_inverse<T, MAXE>, grid, dim3(rl.threads), rl.smem, st, a);
-  }
-  return e;
 }
 
 template <typename T>
 cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLaunch& rl,
-                              cudaStream_t st) {
-  switch (rl.maxe) {
-    case 1: return launch_row_inst<T, 1>(forward, a, grid, rl, st);
-    case 2: return launch_row_inst<T, 2>(forward, a, grid, rl, st);
-    case 4: return launch_row_inst<T, 4>(forward, a, grid, rl, st);
-    case 8: return launch_row_inst<T, 8>(forward, a, grid, rl, st);
-    default: return launch_row_inst<T, 16>(forward, a, grid, rl, st);
+                       cudaStream_t st) {
+  cudaError_t e;
+  if (forward) {
+    if ((e = grant_smem(k_row_forward<T>, rl.smem, RowGrant<T>::f)) != cudaSuccess) return e;
+    return launch_pdl(k_row_forward<T>, grid, dim3(rl.threads), rl.smem, st, a);
   }
+  if ((e = grant_smem(k_row_inverse<T>, rl.smem, RowGrant<T>::i)) != cudaSuccess) return e;
+  return launch_pdl(k_row_inverse<T>, grid, dim3(rl.threads), rl.smem, st, a);
 }
 
 template <typename T>

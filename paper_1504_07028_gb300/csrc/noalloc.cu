@@ -189,7 +189,7 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
   const int col_threads = (2 * CB * ca.NSEG + 31) / 32 * 32;
   const int ncolblk = (Wh * K + CB - 1) / CB;
 
-  const dim3 rg(H, nq);
+  const dim3 rg(nq, H);
   if (launch_row<float>(true, ra, rg, rl, st) != cudaSuccess ||
       launch_col<float>(ca, ncolblk, col_threads, col_smem, st) != cudaSuccess ||
       launch_row<float>(false, ra, rg, rl, st) != cudaSuccess)

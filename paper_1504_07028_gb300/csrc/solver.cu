@@ -217,7 +217,7 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   const bool small_image = (long long)H * W < 65536;
   pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
   if (tl && tl->row_pairs) {
-    const int qmax = row_pairs_per_cta(pl.Mf, Q);  // the most that fit a CTA
+    const int qmax = row_pairs_per_cta(pl.Mf, Q, 1 << 30, 8192 * 4 / (int)sizeof(T));  // the most a CTA takes
     pl.QB = std::min(floor_pow2(tl->row_pairs), qmax);
   }
   pl.nqblk = (Q + pl.QB - 1) / pl.QB;
@@ -519,7 +519,7 @@ class Solver : public SolverBase {
   // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep partials (src == nullptr)
   int z_update(const T* src, T* zout) {
     const RowArgs<T> ra = row_args(src, zout);
-    const dim3 rg(pl.H, pl.nqblk);
+    const dim3 rg(pl.nqblk, pl.H);
     SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
     ColArgs<T> ca{};
     ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG;
