@@ -337,3 +337,25 @@ def labels_and_margin(z: np.ndarray):
     lab = np.argmax(z, axis=0)
     srt = np.sort(z, axis=0)
     return lab, srt[-1] - srt[-2]
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 5: the class model that feeds problem (7). The experiments model the classes with a
+# multinomial logistic regression (MLR); its posterior is the softmax of one affine function
+# of the spectrum per class. The paper prints no formula; this is the standard definition,
+# with an optional bias per class.
+# ------------------------------------------------------------------------------------------
+
+def mlr_probs(x: np.ndarray, Wc: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
+    """p_i = softmax_k(w_k^T x_i + b_k) for spectra x of shape (H, W, d), weights Wc (K, d)
+    and biases b (K,); returns p class-major (K, H, W) like z."""
+    H, W, d = x.shape
+    K = Wc.shape[0]
+    logits = x.reshape(H * W, d) @ Wc.T                      # (n, K), a library matmul
+    if b is not None:
+        logits = logits + b[None, :]
+    logits = logits - logits.max(axis=1, keepdims=True)      # exp of non-positive numbers
+    e = np.exp(logits)
+    p = e / e.sum(axis=1, keepdims=True)
+    return np.ascontiguousarray(p.T.reshape(K, H, W))
+

@@ -126,11 +126,48 @@ def batch_scenes(count: int = 64, seed_base: int = 5000):
     return out
 
 
+@dataclasses.dataclass(frozen=True)
+class MlrScene:
+    """Spectra, MLR weights and labels of a scene whose class probabilities come from a
+    multinomial logistic regression (the class model of the paper's experiments, Sec. 5)."""
+
+    H: int
+    W: int
+    K: int
+    d: int
+    labels: np.ndarray     # (H, W) int64 ground truth
+    x: np.ndarray          # (H, W, d) float64 spectra, pixel-major
+    Wc: np.ndarray         # (K, d) float64 MLR weights
+    b: np.ndarray          # (K,) float64 MLR biases
+
+
+def mlr_scene(H: int, W: int, K: int, d: int, S: int, seed: int) -> MlrScene:
+    """Voronoi labels (as in ``scene``); class means mu_k ~ U(0,1)^d; spectra
+    x_i = mu_{y_i} + N(0, 0.05^2) per band; weights Wc_k = (24/d)(mu_k - mean_j mu_j) +
+    N(0, 1/d) (the first term gives the true class an expected logit margin of about 2, since
+    E|mu_y - mu_k|^2 / 2 = d/12 for uniform means); biases 0. Draw order: labels, means,
+    noise, weight noise."""
+    rng = np.random.default_rng(seed)
+    y = voronoi_labels(rng, H, W, S, K)
+    mu = rng.uniform(0.0, 1.0, size=(K, d))
+    x = mu[y] + rng.normal(0.0, 0.05, size=(H, W, d))
+    Wc = (24.0 / d) * (mu - mu.mean(axis=0, keepdims=True)) + rng.normal(
+        0.0, 1.0 / np.sqrt(d), size=(K, d))
+    return MlrScene(H=H, W=W, K=K, d=d, labels=y, x=x, Wc=Wc, b=np.zeros(K))
+
+
+def scene_610x340_mlr() -> MlrScene:
+    """610x340, K=9 classes, d=103 bands (the shape of a university hyperspectral scene),
+    30 Voronoi seeds (seed 3)."""
+    return mlr_scene(610, 340, 9, 103, S=30, seed=3)
+
+
 CFG_64 = SolverConfig(M=1, sigma=0.5, lam=2.0, mu=1.0, schatten_p=1, iters=200)
 CFG_145 = {sp: SolverConfig(M=1, sigma=0.5, lam=1.5, mu=1.0, schatten_p=sp, iters=300)
            for sp in (1, 2, np.inf)}
 CFG_256 = SolverConfig(M=1, sigma=0.5, lam=2.0, mu=1.0, schatten_p=1, iters=50)
 CFG_BATCH = SolverConfig(M=1, sigma=0.5, lam=2.0, mu=1.0, schatten_p=1, iters=200)
+CFG_MLR = SolverConfig(M=2, sigma=1.0, lam=1.5, mu=1.0, schatten_p=1, iters=400)
 
 
 def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:

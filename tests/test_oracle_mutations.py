@@ -7,7 +7,8 @@ from oracle import segsalsa_str_oracle as O
 import tests.test_oracle_pins as P
 
 _orig = {name: getattr(O, name) for name in
-         ("shift", "prox_g1", "prox_g2", "linear_solve", "prox_g4", "D_v_T", "jacobian")}
+         ("shift", "prox_g1", "prox_g2", "linear_solve", "prox_g4", "D_v_T", "jacobian",
+          "mlr_probs")}
 
 
 def _wrong_shift(f, s):                     # shift sign flipped
@@ -47,6 +48,17 @@ def _dropped_weight(z, omega, M):           # weights dropped from the Jacobian
     return _orig["jacobian"](z, np.ones_like(omega), M)
 
 
+def _dropped_bias(x, Wc, b=None):           # MLR bias ignored
+    return _orig["mlr_probs"](x, Wc, None)
+
+
+def _wrong_softmax_axis(x, Wc, b=None):     # normalised over pixels instead of classes
+    H, W, d = x.shape
+    lg = x.reshape(H * W, d) @ Wc.T + (0 if b is None else b[None, :])
+    e = np.exp(lg - lg.max(axis=0, keepdims=True))
+    return np.ascontiguousarray((e / e.sum(axis=0, keepdims=True)).T.reshape(-1, H, W))
+
+
 MUTATIONS = [
     ("shift", _wrong_shift, [P.test_jacobian_brute_force_loops]),
     ("prox_g1", _wrong_root, [P.test_prox_g1_stationarity]),
@@ -58,6 +70,8 @@ MUTATIONS = [
     ("D_v_T", _wrong_adjoint, [lambda: P.test_jacobian_adjoint(1)]),
     ("jacobian", _dropped_weight, [lambda: P.test_JTJ_equals_weighted_laplacian(1),
                                    lambda: P.test_symbol_closed_form(6, 8, 1)]),
+    ("mlr_probs", _dropped_bias, [P.test_mlr_brute_force]),
+    ("mlr_probs", _wrong_softmax_axis, [P.test_mlr_brute_force, P.test_mlr_special_cases]),
 ]
 
 

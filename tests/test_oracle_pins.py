@@ -337,3 +337,57 @@ def test_fixed_point_is_a_minimiser():
         for _ in range(40):
             zq = O.proj_simplex(z + eps * rng.normal(size=z.shape))
             assert O.objective(zq, sc.p, 0.8, om, 1, 1) >= f0 - 1e-6
+
+
+# ------------------------------------------------------------- Sec. 5: MLR class model
+
+def _mlr_brute(x, Wc, b):
+    """p_k = 1 / sum_j exp(l_j - l_k), pixel by pixel with math.exp (a different formula from
+    the oracle's shifted softmax)."""
+    import math
+    H, W, d = x.shape
+    K = Wc.shape[0]
+    p = np.zeros((K, H, W))
+    for yy in range(H):
+        for xx in range(W):
+            lg = [sum(Wc[k, t] * x[yy, xx, t] for t in range(d)) + b[k] for k in range(K)]
+            for k in range(K):
+                p[k, yy, xx] = 1.0 / sum(math.exp(lj - lg[k]) for lj in lg)
+    return p
+
+
+def test_mlr_brute_force():
+    sc = synth.mlr_scene(3, 4, 5, 7, S=3, seed=40)
+    b = np.random.default_rng(41).normal(size=5)
+    assert np.abs(O.mlr_probs(sc.x, sc.Wc, b) - _mlr_brute(sc.x, sc.Wc, b)).max() < 1e-14
+
+
+def test_mlr_special_cases():
+    sc = synth.mlr_scene(4, 5, 6, 9, S=3, seed=42)
+    # zero weights: uniform posterior
+    assert np.abs(O.mlr_probs(sc.x, np.zeros_like(sc.Wc), np.zeros(6)) - 1.0 / 6).max() < 1e-15
+    # K = 2 is the logistic sigmoid of the logit difference
+    W2, b2 = sc.Wc[:2], np.array([0.3, -0.2])
+    l = sc.x @ W2.T + b2
+    sig = 1.0 / (1.0 + np.exp(-(l[..., 1] - l[..., 0])))
+    assert np.abs(O.mlr_probs(sc.x, W2, b2)[1] - sig).max() < 1e-14
+    # a common shift of the biases changes nothing; sums are one; order follows the logits
+    p = O.mlr_probs(sc.x, sc.Wc, sc.b)
+    assert np.abs(O.mlr_probs(sc.x, sc.Wc, sc.b + 7.5) - p).max() < 1e-14
+    assert np.abs(p.sum(axis=0) - 1.0).max() < 1e-14 and p.min() > 0
+    lg = np.moveaxis(sc.x @ sc.Wc.T, -1, 0)
+    assert np.array_equal(np.argmax(p, axis=0), np.argmax(lg, axis=0))
+    # large weights: one-hot on the logit argmax (no overflow)
+    ph = O.mlr_probs(sc.x, 1e4 * sc.Wc, sc.b)
+    assert np.all(np.isfinite(ph)) and np.abs(ph.max(axis=0) - 1.0).max() < 1e-6
+
+
+def test_mlr_scene_margin():
+    """The synthetic weights give the true class a logit margin of about 2 (recipe check)."""
+    sc = synth.mlr_scene(32, 32, 9, 103, S=12, seed=43)
+    lg = sc.x @ sc.Wc.T
+    y = sc.labels
+    true = np.take_along_axis(lg, y[..., None], axis=-1)[..., 0]
+    other = np.where(np.eye(9, dtype=bool)[y], -np.inf, lg).max(axis=-1)
+    assert 0.5 < np.median(true - other) < 4.0
+    assert np.mean(np.argmax(lg, axis=-1) == y) > 0.6
