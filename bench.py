@@ -217,11 +217,61 @@ def run_reference_batch(args):
     print(json.dumps(line), flush=True)
 
 
+MLR_CROP = (122, 68)   # 1/25 of the 610x340 pixels
+
+
+def oracle_mlr_sample(iters):
+    """FP64 oracle on a 122x68 crop of the MLR workload (same K, d, patch): MLR probabilities
+    plus `iters` iterations. Returns (full-image iterations per second, wall s, cores)."""
+    import torch
+    from oracle import segsalsa_str_oracle as O
+    from paper_1504_07028_gb300 import synth
+    sc = synth.scene_610x340_mlr()
+    cfg = synth.CFG_MLR
+    ch, cw = MLR_CROP
+    xc = np.ascontiguousarray(sc.x[:ch, :cw])
+    x = torch.from_numpy(xc.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    w = torch.from_numpy(sc.Wc.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    t0, c0 = time.perf_counter(), time.process_time()
+    O.solve(O.mlr_probs(x, w), cfg.M, cfg.sigma, cfg.lam, cfg.mu, cfg.schatten_p, iters)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    scale = (ch * cw) / (sc.H * sc.W)
+    return iters * scale / wall, wall, max(1, round(cpu / wall))
+
+
+def run_reference_mlr(args):
+    per = max(1, args.ref_iters)
+    for _ in range(args.warmup):
+        oracle_mlr_sample(1)
+    rates, walls, cores = [], 0.0, 1
+    for _ in range(args.steps):
+        r, wall, cores = oracle_mlr_sample(per)
+        rates.append(r)
+        walls += wall
+    v = float(np.mean(rates))
+    tot_t = walls
+    sample = (f"MLR probabilities + {per} iterations of a {MLR_CROP[0]}x{MLR_CROP[1]} crop per "
+              f"step ({args.steps} steps), scaled to the 610x340 image by pixel count")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ADMM iter/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": MLR_DESC, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     if args.workload == "batch64":
         run_reference_batch(args)
+        return
+    if args.workload == "mlr610x340":
+        run_reference_mlr(args)
         return
     sc, cfgs, desc = make_workload(args.workload)
     per_p = max(1, args.ref_iters)
@@ -614,6 +664,158 @@ def run_batch(args, rank, world, local_rank):
     bt.close()
 
 
+MLR_DESC = ("610x340 K=9, d=103 bands, MLR class model p = softmax(W x) as BF16 tensor-core GEMM "
+            "(FP32 accumulation) + softmax, 5x5 Gaussian patch sigma=1, lambda=1.5, mu=1, Schatten "
+            "p=1, 400 iterations")
+
+
+def run_mlr(args, rank, world, local_rank):
+    """Mixed-precision workload with the MLR front end. One step = set_spectra (BF16 spectra and
+    weights resident on the device: tensor-core GEMM + softmax + validation + init), 400 FP32
+    SALSA iterations with the trace every 10, label readout. value = ADMM iterations/s."""
+    import torch
+    from paper_1504_07028_gb300 import binding as B
+    from paper_1504_07028_gb300 import build as Bu
+    from paper_1504_07028_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    Bu.build()
+    sc = synth.scene_610x340_mlr()
+    cfg = synth.CFG_MLR
+    H, W, K, d = sc.H, sc.W, sc.K, sc.d
+    n = H * W
+    mk = lambda prec: B.make_params(H, W, K, M=cfg.M, sigma=cfg.sigma, lam=cfg.lam, mu=cfg.mu,
+                                    schatten_p=cfg.schatten_p, precision=prec)
+    s = B.Solver(mk("fp32"))
+    xh = torch.from_numpy(sc.x.astype(np.float32)).to(torch.bfloat16)
+    wh = torch.from_numpy(sc.Wc.astype(np.float32)).to(torch.bfloat16)
+    xd, wd = xh.to(dev), wh.to(dev)
+    lab = torch.empty((H, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+
+    def step(x, w, out):
+        s.set_spectra(x, w)
+        s.solve(cfg.iters, trace_every=10)
+        s.get_labels(out)
+
+    for _ in range(args.warmup):
+        step(xd, wd, lab)
+    torch.cuda.synchronize()
+    s.reset_stats()
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(xd, wd, lab)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = max_over_ranks(float(sum(times)), dev)
+    launches = sum(c for c, _ in s.kernel_stats().values())
+    value = whole_job_rate(cfg.iters * args.steps, world, total_ms * 1e-3)
+    # per-kernel device times: a profiled (eager) replay of the timed steps
+    s.reset_stats()
+    s.set_profiling(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step(xd, wd, lab)
+    stats = s.kernel_stats()
+    s.set_profiling(False)
+    hbm_peak, peak_kind = _peaks()
+    sweep_bytes, _ = s.traffic_model()
+    sw_cnt, sw_ms = stats["sweep"]
+    achieved = sweep_bytes / (sw_ms / sw_cnt * 1e-3) / 1e9
+    ml_cnt, ml_ms = stats["mlr"]
+    dpad, npad = (d + 15) // 16 * 16, (16 if K <= 16 else 32)
+    mlr_bytes = n * d * 2 + K * d * 2 + n * K * 4
+    mlr_s = ml_ms / ml_cnt * 1e-3
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    # end to end with host buffers (pinned BF16 spectra and weights in, labels out)
+    xp = xh.view(torch.int16).pin_memory()
+    wp = wh.view(torch.int16).pin_memory()
+    xp_np, wp_np = xp.numpy().view(np.uint16), wp.numpy().view(np.uint16)
+    labh = torch.empty((H, W), dtype=torch.int32).pin_memory()
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(xp_np, wp_np, labh)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e), dev)
+    e2e_value = whole_job_rate(cfg.iters * len(e2e), world, e2e_s)
+    # accuracy against the FP64 GPU path from the same BF16 inputs
+    err, lab_ok = 0.0, True
+    if rank == 0 and not args.skip_fp64_check:
+        s.set_spectra(xd, wd)
+        s.solve(cfg.iters)
+        z32 = s.get_z()
+        s64 = B.Solver(mk("fp64"))
+        s64.set_spectra(xd, wd)
+        s64.solve(cfg.iters)
+        z64 = s64.get_z()
+        s64.close()
+        err = float(np.abs(z32 - z64).max())
+        srt = np.sort(z64, axis=0)
+        clear = srt[-1] - srt[-2] >= 1e-3
+        lab_ok = bool(np.array_equal(np.argmax(z32, 0)[clear], np.argmax(z64, 0)[clear]))
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        it = max(1, args.cpu_iters)
+        v_cpu, wall, cores = oracle_mlr_sample(it)
+        cpu = {"value": v_cpu, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
+               "sample": f"MLR probabilities + {it} iterations of a {MLR_CROP[0]}x{MLR_CROP[1]} "
+                         f"crop ({wall:.1f} s), scaled to the full image by pixel count"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic",
+        "config": {"workload": MLR_DESC, "H": H, "W": W, "K": K, "d": d, "iters_per_step": cfg.iters,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "mpixel_class_iter_per_s": value * n * K / 1e6,
+        "accuracy": {"max_abs_z_vs_fp64": err, "labels_match_off_1e-3_margin": lab_ok},
+        "roofline": {"bound": "hbm", "kernel": "sweep (fused prox + dual + rhs partials)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": sweep_bytes,
+                     "avg_launch_us": sw_ms / sw_cnt * 1e3},
+        "mlr_kernel": {"bound": "hbm", "avg_launch_us": mlr_s * 1e6,
+                       "algorithmic_bytes": mlr_bytes, "achieved_gbs": mlr_bytes / mlr_s / 1e9,
+                       "frac_of_hbm": mlr_bytes / mlr_s / 1e9 / hbm_peak,
+                       "tensor_flops": 2 * n * dpad * npad,
+                       "achieved_tflops": 2 * n * dpad * npad / mlr_s / 1e12},
+        "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
+        "kernel_timing": "CUDA events around every launch on the launch stream, in an eager "
+                         "replay of the timed steps",
+        "dominant_kernel": dom[0],
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "ADMM iter/s", "h2d_bytes_per_step": n * d * 2 + K * d * 2,
+                "d2h_bytes_per_step": 4 * n + 48 * (cfg.iters // 10 + 1)},
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -622,7 +824,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="145x145",
                     help="145x145 (default), 64x64, 2048x2048, HxW (K=16 synthetic scene), or "
-                         "batch64 (64 uneven images in one batch)")
+                         "batch64 (64 uneven images in one batch), or mlr610x340 (MLR front end)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tilings")
     ap.add_argument("--tune-iters", type=int, default=4, help="batch64: iterations per trial")
     ap.add_argument("--cpu-iters", type=int, default=8)
@@ -646,6 +848,8 @@ def main():
     try:
         if args.workload == "batch64":
             run_batch(args, rank, world, local_rank)
+        elif args.workload == "mlr610x340":
+            run_mlr(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

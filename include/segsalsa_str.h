@@ -139,6 +139,23 @@ int segsalsa_str_set_state(segsalsa_str_t* h, const void* z, const void* d1, con
  * rhs and z pixel-major (H, W, K). Leaves the solver state untouched. */
 int segsalsa_str_linear_solve(segsalsa_str_t* h, const void* rhs, void* z, int32_t on_device);
 
+/* Class model of the experiments (Sec. 5: the classes are modelled by a multinomial logistic
+ * regression, MLR) as the source of p: p_i = softmax_k(w_k^T x_i + b_k), then everything
+ * set_probs does (validation, z^0 = p_i, d^0 = 0, iteration counter 0).
+ *  - x: H*W*d BF16 values as raw 16-bit patterns, pixel-major (H, W, d); w: K*d BF16 values,
+ *    (K, d); bias: K floats, or NULL for zeros. All three in host memory (on_device = 0) or
+ *    all in device memory (on_device = 1); they are not kept after the call.
+ *  - 1 <= d <= 256 (bands). The contraction runs on the tensor cores (tcgen05, BF16 inputs,
+ *    FP32 accumulation), the bias and softmax in FP32; p is stored in the handle's precision.
+ *  - Non-finite spectra or weights give non-finite p: SEGSALSA_ERR_ARG, state unchanged.
+ *    SEGSALSA_ERR_TIMEOUT if the kernel's bounded wait on the tensor core gave up. */
+int segsalsa_str_set_spectra(segsalsa_str_t* h, const void* x, const void* w, const float* bias,
+                             int32_t d, int32_t on_device);
+
+/* The class probabilities p of the current solve (set by set_probs or set_spectra), H*W*K
+ * elements in `layout`, in the handle's precision. */
+int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t on_device);
+
 /* Allocation-free z-update. The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory (code running under a fixed memory budget or an outside
  * allocator, or a plug-in without a handle). It solves (3 I + c (D_h^T D_h + D_v^T D_v)) z = rhs
@@ -163,8 +180,9 @@ int segsalsa_str_linear_solve_static(const float* rhs, float* z, int32_t H, int3
  * solve() so that kernel_stats() can report, per kernel kind, the launch count and the total
  * device time in milliseconds since the last reset. Kernel kinds (index):
  *   0 fused sweep (prox + dual + rhs partials), 1 row FFT forward (with partial gather),
- *   2 column solve, 3 row FFT inverse, 4 diagnostics (residual / objective), 5 other.
- * launches and ms point to arrays of at least 6 entries (host memory). kernel_stats works
+ *   2 column solve, 3 row FFT inverse, 4 diagnostics (residual / objective), 5 other,
+ *   6 MLR class model (set_spectra).
+ * launches and ms point to arrays of at least 7 entries (host memory). kernel_stats works
  * with profiling off too; then ms is not filled. reset_stats zeroes both. */
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on);
 int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms);

@@ -27,7 +27,7 @@ SEGSALSA_LAYOUT_HWK = 1
 SEGSALSA_SCHATTEN_INF = 0
 
 KERNEL_KINDS = ("sweep", "row_fft_forward", "column_solve", "row_fft_inverse", "diagnostics",
-                "other")
+                "other", "mlr")
 
 SYMBOLS = (
     "segsalsa_str_workspace_bytes", "segsalsa_str_create", "segsalsa_str_set_probs",
@@ -40,6 +40,7 @@ SYMBOLS = (
     "segsalsa_str_batch_create", "segsalsa_str_batch_image", "segsalsa_str_batch_solve",
     "segsalsa_str_batch_autotune", "segsalsa_str_batch_set_lanes", "segsalsa_str_batch_get_lanes",
     "segsalsa_str_batch_destroy", "segsalsa_str_batch_last_error",
+    "segsalsa_str_set_spectra", "segsalsa_str_get_probs",
 )
 
 
@@ -121,6 +122,8 @@ def load(path: str | None = None):
         "segsalsa_str_batch_set_lanes": (C.c_int, [vp, i32]),
         "segsalsa_str_batch_get_lanes": (C.c_int, [vp, C.POINTER(i32)]),
         "segsalsa_str_batch_destroy": (None, [vp]),
+        "segsalsa_str_set_spectra": (C.c_int, [vp, vp, vp, vp, i32, i32]),
+        "segsalsa_str_get_probs": (C.c_int, [vp, vp, i32, i32]),
         "segsalsa_str_batch_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -147,6 +150,23 @@ def _ptr(a, dtype):
     tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}
     if a.dtype != tmap[np.dtype(dtype).type]:
         raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), int(a.is_cuda)
+
+
+def _ptr_bf16(a):
+    """(pointer, on_device) of a contiguous BF16 array: a torch.bfloat16 tensor or a numpy
+    uint16 array holding BF16 bit patterns."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.uint16:
+            raise TypeError("numpy BF16 data must be uint16 bit patterns")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    import torch
+    if a.dtype != torch.bfloat16:
+        raise TypeError(f"expected torch.bfloat16, got {a.dtype}")
     if not a.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return a.data_ptr(), int(a.is_cuda)
@@ -289,6 +309,31 @@ class Solver:
         self._c(self.lib.segsalsa_str_solve(self.h, int(iters), None, 0, None))
         return None
 
+    # segsalsa_str_set_spectra
+    def set_spectra(self, x, w, bias=None):
+        """x: (H, W, d) BF16, w: (K, d) BF16 (torch.bfloat16 or numpy uint16 bit patterns),
+        bias: (K,) float32 or None; x, w and bias on the same side (host or device)."""
+        d = int(x.shape[-1])
+        if tuple(x.shape) != (self.H, self.W, d) or tuple(w.shape) != (self.K, d):
+            raise ValueError("x must be (H, W, d) and w (K, d)")
+        px_, dx = _ptr_bf16(x)
+        pw, dw = _ptr_bf16(w)
+        pb, db = (None, dx)
+        if bias is not None:
+            pb, db = _ptr(bias, np.float32)
+        if not (dx == dw == db):
+            raise ValueError("x, w and bias must all be host or all device arrays")
+        self._c(self.lib.segsalsa_str_set_spectra(self.h, px_, pw, pb, d, dx))
+
+    # segsalsa_str_get_probs
+    def get_probs(self, out=None, layout=SEGSALSA_LAYOUT_KHW):
+        if out is None:
+            shape = (self.K, self.H, self.W) if layout == SEGSALSA_LAYOUT_KHW else (self.H, self.W, self.K)
+            out = np.empty(shape, dtype=self.dtype)
+        ptr, dev = _ptr(out, self.dtype)
+        self._c(self.lib.segsalsa_str_get_probs(self.h, ptr, layout, dev))
+        return out
+
     # segsalsa_str_get_labels
     def get_labels(self, out=None):
         if out is None:
@@ -346,10 +391,10 @@ class Solver:
         self._c(self.lib.segsalsa_str_set_profiling(self.h, int(bool(on))))
 
     def kernel_stats(self):
-        n = (C.c_int64 * 6)()
-        ms = (C.c_double * 6)()
+        n = (C.c_int64 * len(KERNEL_KINDS))()
+        ms = (C.c_double * len(KERNEL_KINDS))()
         self._c(self.lib.segsalsa_str_kernel_stats(self.h, n, ms))
-        return {KERNEL_KINDS[i]: (int(n[i]), float(ms[i])) for i in range(6)}
+        return {KERNEL_KINDS[i]: (int(n[i]), float(ms[i])) for i in range(len(KERNEL_KINDS))}
 
     def reset_stats(self):
         self._c(self.lib.segsalsa_str_reset_stats(self.h))

@@ -24,11 +24,13 @@
 #include "aux.cuh"
 #include "fft.cuh"
 #include "launch.h"
+#include "mlr.cuh"
 
 namespace sgs {
 
-enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIAG = 4, KIND_OTHER = 5 };
-constexpr int NKIND = 6;
+enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIAG = 4, KIND_OTHER = 5,
+            KIND_MLR = 6 };
+constexpr int NKIND = 7;
 constexpr int MAXCOV = 2;           // tile covers per row / column in the partial gather
 constexpr int TRACE_CAP = 128;      // device trace records before a flush to the host
 
@@ -48,6 +50,8 @@ struct SolverBase {
   virtual int set_state(const void* z, const void* d1, const void* d2, const void* d3,
                         const void* d4, const void* rhs, int k, int dev) = 0;
   virtual int linear_solve(const void* rhs, void* z, int dev) = 0;
+  virtual int set_spectra(const void* x, const void* w, const float* bias, int d, int dev) = 0;
+  virtual int get_probs(void* p, int layout, int dev) = 0;
   virtual int set_profiling(int on) = 0;
   virtual int kernel_stats(int64_t* launches, double* ms) = 0;
   virtual int reset_stats() = 0;
@@ -358,6 +362,8 @@ class Solver : public SolverBase {
   };
   std::map<std::pair<int, int>, Chunk> chunks;
   double* trace_host = nullptr;  // pinned staging for trace records
+  void* mlr_buf = nullptr;       // device staging of host spectra / weights / biases
+  size_t mlr_cap = 0;
   int trace_host_cap = 0;
   bool use_graphs = true;
 
@@ -366,6 +372,7 @@ class Solver : public SolverBase {
     for (auto& kv : chunks)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (trace_host) cudaFreeHost(trace_host);
+    if (mlr_buf) cudaFree(mlr_buf);
     for (auto& e : evs) { cudaEventDestroy(std::get<1>(e)); cudaEventDestroy(std::get<2>(e)); }
     for (auto e : evpool) cudaEventDestroy(e);
     if (own_ws && ws) cudaFree(ws);
@@ -574,6 +581,13 @@ class Solver : public SolverBase {
       if ((rc = copy_in(b.zp, p, nK, dev))) return rc;
       SGS_LAUNCH(KIND_OTHER, (k_khw_to_hwk<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.zp, b.tmp, n, K)));
     }
+    return commit_probs();
+  }
+
+  // Validate the probabilities staged in b.tmp (pixel-major) and start a new solve from them.
+  int commit_probs() {
+    const int n = pl.n, K = pl.K;
+    const size_t nK = (size_t)n * K;
     SGS_CUDA(cudaMemsetAsync(b.flag, 0, sizeof(int), st));
     SGS_LAUNCH(KIND_OTHER, (k_check_probs<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.tmp, n, K, b.flag)));
     int flag = 0;
@@ -590,6 +604,65 @@ class Solver : public SolverBase {
     iter = 0;
     rhs_dense = false;
     have_probs = true;
+    return SEGSALSA_OK;
+  }
+
+  int set_spectra(const void* x, const void* w, const float* bias, int d, int dev) override {
+    if (!x || !w) return fail(SEGSALSA_ERR_ARG, "x and w are required");
+    if (d < 1 || d > MLR_MAXD) return fail(SEGSALSA_ERR_ARG, "d must be in [1, 256]");
+    const size_t n = (size_t)pl.n, K = (size_t)pl.K;
+    const size_t xb = n * d * 2, wb = K * d * 2, bb = K * sizeof(float);
+    const uint16_t* xd = static_cast<const uint16_t*>(x);
+    const uint16_t* wd = static_cast<const uint16_t*>(w);
+    const float* bd = bias;
+    if (!dev) {
+      const size_t need = align_up(xb, 256) + align_up(wb, 256) + bb;
+      if (need > mlr_cap) {
+        if (mlr_buf) cudaFree(mlr_buf);
+        mlr_buf = nullptr;
+        mlr_cap = 0;
+        cudaError_t e = cudaMalloc(&mlr_buf, need);
+        if (e != cudaSuccess) { mlr_buf = nullptr; return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        mlr_cap = need;
+      }
+      char* base = static_cast<char*>(mlr_buf);
+      SGS_CUDA(cudaMemcpyAsync(base, x, xb, cudaMemcpyHostToDevice, st));
+      SGS_CUDA(cudaMemcpyAsync(base + align_up(xb, 256), w, wb, cudaMemcpyHostToDevice, st));
+      xd = reinterpret_cast<const uint16_t*>(base);
+      wd = reinterpret_cast<const uint16_t*>(base + align_up(xb, 256));
+      if (bias) {
+        float* bdev = reinterpret_cast<float*>(base + align_up(xb, 256) + align_up(wb, 256));
+        SGS_CUDA(cudaMemcpyAsync(bdev, bias, bb, cudaMemcpyHostToDevice, st));
+        bd = bdev;
+      }
+    }
+    MlrArgs a{};
+    a.x = xd; a.w = wd; a.bias = bd; a.p = b.tmp; a.err = b.err;
+    a.n = pl.n; a.d = d; a.dpad = (d + 15) / 16 * 16; a.K = pl.K; a.npad = pl.K <= 16 ? 16 : 32;
+    SGS_CUDA(launch(KIND_MLR, [&]() { return launch_mlr<T>(a, st); }));
+    int errflag = 0;
+    SGS_CUDA(cudaMemcpyAsync(&errflag, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    if (errflag) {
+      cudaMemsetAsync(b.err, 0, sizeof(int), st);
+      return fail(SEGSALSA_ERR_TIMEOUT, "the tensor-core wait gave up (bounded wait exceeded)");
+    }
+    return commit_probs();
+  }
+
+  int get_probs(void* p, int layout, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "no state: call set_probs first");
+    if (!p) return fail(SEGSALSA_ERR_ARG, "p is NULL");
+    if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_out(p, b.p, nK, dev))) return rc;
+    } else {
+      SGS_LAUNCH(KIND_OTHER, (k_hwk_to_khw<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.p, b.tmp, pl.n, pl.K)));
+      if ((rc = copy_out(p, b.tmp, nK, dev))) return rc;
+    }
+    SGS_CUDA(cudaStreamSynchronize(st));
     return SEGSALSA_OK;
   }
 
@@ -643,6 +716,7 @@ class Solver : public SolverBase {
   int ensure_trace_host(int n) {
     if (n <= trace_host_cap) return SEGSALSA_OK;
     if (trace_host) cudaFreeHost(trace_host);
+    if (mlr_buf) cudaFree(mlr_buf);
     trace_host = nullptr;
     trace_host_cap = 0;
     SGS_CUDA(cudaMallocHost(&trace_host, sizeof(double) * 6 * (size_t)n));
@@ -1431,6 +1505,13 @@ int segsalsa_str_set_state(segsalsa_str_t* h, const void* z, const void* d1, con
 }
 int segsalsa_str_linear_solve(segsalsa_str_t* h, const void* rhs, void* z, int32_t dev) {
   SGS_H(h); return h->impl->linear_solve(rhs, z, dev);
+}
+int segsalsa_str_set_spectra(segsalsa_str_t* h, const void* x, const void* w, const float* bias,
+                             int32_t d, int32_t dev) {
+  SGS_H(h); return h->impl->set_spectra(x, w, bias, d, dev);
+}
+int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t dev) {
+  SGS_H(h); return h->impl->get_probs(p, layout, dev);
 }
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on) {
   SGS_H(h); return h->impl->set_profiling(on);
