@@ -51,14 +51,11 @@ struct SweepArgs {
 // [[a, b], [b, c]] = V^T V. With V = U diag(s) W^T and shrunk values t, u2 = V W diag(g) W^T,
 // g_i = t_i / s_i. Writing W diag(g) W^T = gbar I + kap [[hd, b], [b, -hd]], hd = (a - c)/2,
 // kap = (g1 - g2) / (l1 - l2), the case formulas below have no cancellation at s1 = s2.
-// Mixed precision: an FP32 sweep evaluates the eigen-decomposition of a near-degenerate Gram
-// matrix (eigenvalue gap below 1e-6 of the trace) in FP64; for a symmetric 2 x 2 matrix that
-// decomposition is exactly one Jacobi rotation, whose angle and eigenvalues the closed form
-// computes. Elsewhere the FP32 evaluation stands (FP64 throughput is low on this part, and
-// the sweep is bound by memory bandwidth).
-static __device__ __noinline__ void schatten_coeffs_fp64(float a, float b, float c, float tau, int sp,
-                                                 float& A11, float& A12, float& A22);
-
+// The eigen-decomposition of the symmetric 2 x 2 Gram matrix is one Jacobi rotation; the
+// closed form needs no rotation angle, and where both singular values are shrunk (or both
+// kept) no division by the eigenvalue gap, so it stays accurate in FP32 when the two values
+// coincide. Where exactly one is shrunk, kap = g1 / (2 r) is a bounded ratio whose two factors
+// vanish together (g1 <= (s1 - s2) / s1).
 template <typename T>
 __device__ __forceinline__ void schatten_coeffs(T a, T b, T c, T tau, int sp, T& A11, T& A12,
                                                 T& A22) {
@@ -70,12 +67,6 @@ __device__ __forceinline__ void schatten_coeffs(T a, T b, T c, T tau, int sp, T&
     gbar = (nf > tau) ? T(1) - tau / nf : T(0);
   } else if (tr > T(0)) {
     const T r = sqrt(hd * hd + b * b);             // (l1 - l2) / 2
-    if constexpr (sizeof(T) == 4) {
-      if (r < T(5e-7) * tr) {                       // gap l1 - l2 = 2 r below 1e-6 tr
-        schatten_coeffs_fp64(a, b, c, tau, sp, A11, A12, A22);
-        return;
-      }
-    }
     const T l1 = T(0.5) * tr + r;
     const T l2 = fmax(T(0.5) * tr - r, T(0));
     const T s1 = sqrt(l1), s2 = sqrt(l2);
@@ -111,17 +102,6 @@ __device__ __forceinline__ void schatten_coeffs(T a, T b, T c, T tau, int sp, T&
   A11 = gbar + kap * hd;
   A22 = gbar - kap * hd;
   A12 = kap * b;
-}
-
-// The near-degenerate case of an FP32 sweep, evaluated in FP64 (kept out of line so that the
-// common path keeps its registers).
-static __device__ __noinline__ void schatten_coeffs_fp64(float a, float b, float c, float tau, int sp,
-                                                 float& A11, float& A12, float& A22) {
-  double d11, d12, d22;
-  schatten_coeffs<double>((double)a, (double)b, (double)c, (double)tau, sp, d11, d12, d22);
-  A11 = (float)d11;
-  A12 = (float)d12;
-  A22 = (float)d22;
 }
 
 template <typename T> struct Vec2Of;

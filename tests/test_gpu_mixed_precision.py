@@ -1,5 +1,5 @@
-"""Mixed precision in the FP32 sweep: Gram matrices of the patch Jacobian with (near-)equal
-eigenvalues take the FP64 evaluation of the Schatten prox coefficients.
+"""Degenerate Gram matrices in the FP32 sweep: the closed-form Schatten prox coefficients have
+no division by the eigenvalue gap, so the FP32 path stays accurate when s1 = s2.
 
 Class 0 rising along x and class 1 along y by exactly 1/64 per pixel make every pixel's Gram
 matrix a multiple of the identity away from the wrap-around rows and columns (a = c exactly,
