@@ -134,6 +134,13 @@ def make_workload(name):
         cfgs = [synth.CFG_145[sp] for sp in SP_LIST]
         desc = ("145x145 K=16, 3x3 Gaussian patch sigma=0.5, lambda=1.5, mu=1, 300 iterations "
                 "for each Schatten p in {1,2,inf}")
+    elif name == "patchsweep":
+        sc = synth.scene_145x145_k16()
+        cfgs = [synth.SolverConfig(M=m, sigma=(0.5 if m == 1 else 1.0), lam=1.5, mu=1.0,
+                                   schatten_p=1, iters=300) for m in (0, 1, 2)]
+        desc = ("145x145 K=16, Schatten p=1, lambda=1.5, mu=1, 300 iterations for each patch "
+                "1x1, 3x3 (sigma 0.5) and 5x5 (sigma 1): time against L (Fig. 1's patch sweep "
+                "without the dataset)")
     elif name == "64x64":
         sc = synth.scene_64x64_k4()
         cfgs = [synth.CFG_64]
@@ -399,16 +406,27 @@ def run_ours(args, rank, world, local_rank):
             b.synchronize()
             prof_ms += a.elapsed_time(b)
     stats = {}
-    for _, s in solvers:
-        for kname, (cnt, ms) in s.kernel_stats().items():
+    hbm_peak, peak_kind = _peaks()
+    per_solve = []
+    sw_bytes_tot = 0.0
+    for cfg, s in solvers:
+        st = s.kernel_stats()
+        for kname, (cnt, ms) in st.items():
             c0, m0 = stats.get(kname, (0, 0.0))
             stats[kname] = (c0 + cnt, m0 + ms)
+        sb, ib = s.traffic_model()
+        c_sw, m_sw = st["sweep"]
+        sw_bytes_tot += sb * c_sw
+        per_solve.append({
+            "M": cfg.M, "L": (2 * cfg.M + 1) ** 2, "schatten_p": str(cfg.schatten_p),
+            "sweep_us": m_sw / c_sw * 1e3, "sweep_gbs": sb / (m_sw / c_sw * 1e-3) / 1e9,
+            "sweep_frac_of_hbm": sb / (m_sw / c_sw * 1e-3) / 1e9 / hbm_peak,
+            "kernel_ms_per_iteration": sum(m for _, m in st.values()) / (args.steps * cfg.iters)})
         s.set_profiling(args.profile_run)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     sweep_bytes, iter_bytes = solvers[0][1].traffic_model()
     sw_cnt, sw_ms = stats["sweep"]
-    hbm_peak, peak_kind = _peaks()
-    achieved = sweep_bytes / (sw_ms / sw_cnt * 1e-3) / 1e9
+    achieved = sw_bytes_tot / (sw_ms * 1e-3) / 1e9
     value = whole_job_rate(iters_per_step * args.steps, world, total_ms * 1e-3)
     mpix = value * n * K / 1e6
 
@@ -472,9 +490,10 @@ def run_ours(args, rank, world, local_rank):
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_source": peak_kind,
                      "traffic": _sweep_traffic(args.workload),
-                     "algorithmic_bytes_per_launch": sweep_bytes,
+                     "algorithmic_bytes_per_launch": sw_bytes_tot / sw_cnt,
                      "avg_launch_us": sw_ms / sw_cnt * 1e3},
         "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
+        "per_solve": per_solve,
         "kernel_timing": ("CUDA events around every launch on the launch stream, in a replay "
                           f"of the {args.steps} timed steps with the solves run one at a time "
                           f"({prof_ms:.1f} ms with the events)"),
@@ -825,7 +844,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="145x145",
-                    help="145x145 (default), 64x64, 2048x2048, HxW (K=16 synthetic scene), or "
+                    help="145x145 (default), 64x64, 2048x2048, HxW (K=16 synthetic scene), patchsweep, or "
                          "batch64 (64 uneven images in one batch), or mlr610x340 (MLR front end)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tilings")
     ap.add_argument("--tune-iters", type=int, default=4, help="batch64: iterations per trial")

@@ -63,6 +63,7 @@ typedef enum {
 enum { SEGSALSA_FP32 = 0, SEGSALSA_FP64 = 1 };
 enum { SEGSALSA_LAYOUT_KHW = 0, SEGSALSA_LAYOUT_HWK = 1 };
 enum { SEGSALSA_SCHATTEN_INF = 0 }; /* schatten_p value meaning p = infinity */
+enum { SEGSALSA_G4_AFFINE = 0, SEGSALSA_G4_SIMPLEX = 1 }; /* segsalsa_str_set_g4 modes */
 
 /* Problem statement of eq. (7) and the SALSA penalty of eq. (13). */
 typedef struct {
@@ -110,6 +111,25 @@ int segsalsa_str_set_probs(segsalsa_str_t* h, const void* p, int32_t layout, int
  * Returns SEGSALSA_ERR_NUMERIC if non-finite values appear in a traced record. */
 int segsalsa_str_solve(segsalsa_str_t* h, int32_t iters, double* trace, int32_t trace_every,
                        int32_t* n_records);
+
+/* Residual-based stopping (Sec. 4: the iteration stops once the primal and dual residuals are
+ * below a threshold). Runs traced blocks of check_every >= 1 iterations (the last block may be
+ * shorter) until the record after a block has primal residual <= tol_primal and dual residual
+ * <= tol_dual (the residuals of segsalsa_str_solve's trace records), or max_iters >= 0
+ * iterations have run. *iters_done (nullable) receives the iterations run by this call;
+ * last_record (nullable, host, 6 doubles) the last trace record (NaN if none was written). The
+ * tolerances must be finite and >= 0; 0 runs max_iters iterations unless a residual is 0. */
+int segsalsa_str_solve_until(segsalsa_str_t* h, int32_t max_iters, double tol_primal,
+                             double tol_dual, int32_t check_every, int32_t* iters_done,
+                             double* last_record);
+
+/* Which set g4 indicates (eqs. 10-11). SEGSALSA_G4_AFFINE (the default): the affine set
+ * {1^T xi = 1} as eq. (10) defines g4, whose MPO is the affine projection. SEGSALSA_G4_SIMPLEX:
+ * the probability simplex, whose MPO is the simplex projection, as Sec. 4 describes the MPO of
+ * g4. With g3 = i_+ in both, the two splittings constrain z to the same simplex and reach the
+ * same minimum of (7) by different iterates. Takes effect from the next iteration; the state is
+ * kept. SEGSALSA_ERR_ARG for another mode. */
+int segsalsa_str_set_g4(segsalsa_str_t* h, int32_t mode);
 
 /* Label readout argmax_k z_k of every pixel (link p(y_i = k | z_i) = [z_i]_k, Sec. 2; ties to
  * the lowest k), H*W int32 in row-major pixel order. */

@@ -273,9 +273,13 @@ def initial_state(p: np.ndarray, omega, M) -> SalsaState:
     return SalsaState(z0, u0, d0, 0)
 
 
-def u_d_update(z, d, p, lam, mu, omega, M, sp):
+def u_d_update(z, d, p, lam, mu, omega, M, sp, g4="affine"):
     """Eqs. (13)-(14) given z^{k+1}: the four decoupled MPOs at v = G z^{k+1} - d^k, then
-    d^{k+1} = d^k - (G z^{k+1} - u^{k+1}). Returns (u^{k+1}, d^{k+1}, G z^{k+1})."""
+    d^{k+1} = d^k - (G z^{k+1} - u^{k+1}). Returns (u^{k+1}, d^{k+1}, G z^{k+1}).
+
+    g4 = "affine": the MPO of g4 as eq. (10) defines it (projection onto 1^T xi = 1);
+    g4 = "simplex": the projection onto the probability simplex, as Sec. 4's text describes the
+    MPO of g4 (with g3 = i_+ also present, both variants constrain z to the same feasible set)."""
     L = len(omega)
     K, H, W = p.shape
     Gz = apply_G(z, omega, M)
@@ -284,18 +288,18 @@ def u_d_update(z, d, p, lam, mu, omega, M, sp):
     V2 = jacobian_matrices(v[1])
     u2 = from_jacobian_matrices(prox_g2(V2, lam / mu, sp), L, K, H, W)
     u3 = prox_g3(v[2])
-    u4 = prox_g4(v[3])
+    u4 = prox_g4(v[3]) if g4 == "affine" else proj_simplex(v[3])
     u = [u1, u2, u3, u4]
     dn = [dj - (gj - uj) for dj, gj, uj in zip(d, Gz, u)]
     return u, dn, Gz
 
 
-def salsa_step(st: SalsaState, p, lam, mu, omega, M, sp):
+def salsa_step(st: SalsaState, p, lam, mu, omega, M, sp, g4="affine"):
     """One SALSA iteration (12)-(14). Returns (new state, primal residual, dual residual)."""
     # (12) z^{k+1} = argmin ||G z - u^k - d^k||^2  <=>  G^T G z = G^T (u^k + d^k)
     z = linear_solve(st.rhs(omega, M), omega, M)
     # (13), (14)
-    u, d, Gz = u_d_update(z, st.d, p, lam, mu, omega, M, sp)
+    u, d, Gz = u_d_update(z, st.d, p, lam, mu, omega, M, sp, g4)
     primal = _norm2([gj - uj for gj, uj in zip(Gz, u)])
     dual = mu * _norm2([apply_GT([a - b for a, b in zip(u, st.u)], omega, M)])
     return SalsaState(z, u, d, st.k + 1), primal, dual
@@ -311,7 +315,7 @@ def diagnostics(st: SalsaState, p, lam, omega, M, sp) -> dict:
     }
 
 
-def solve(p, M, sigma, lam, mu, sp, iters, omega=None, trace_every=0, state=None):
+def solve(p, M, sigma, lam, mu, sp, iters, omega=None, trace_every=0, state=None, g4="affine"):
     """Run `iters` SALSA iterations from z^0 = p (normalised) or from `state`.
 
     Returns (state, trace) where trace rows are
@@ -324,7 +328,7 @@ def solve(p, M, sigma, lam, mu, sp, iters, omega=None, trace_every=0, state=None
     st = initial_state(p, omega, M) if state is None else state
     trace = []
     for it in range(iters):
-        st, r, s = salsa_step(st, p, lam, mu, omega, M, sp)
+        st, r, s = salsa_step(st, p, lam, mu, omega, M, sp, g4)
         if trace_every and (st.k % trace_every == 0 or it == iters - 1):
             dg = diagnostics(st, p, lam, omega, M, sp)
             trace.append((st.k, r, s, dg["objective"], dg["min_z"], dg["max_sum_dev"]))

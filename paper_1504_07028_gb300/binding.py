@@ -25,6 +25,8 @@ SEGSALSA_FP64 = 1
 SEGSALSA_LAYOUT_KHW = 0
 SEGSALSA_LAYOUT_HWK = 1
 SEGSALSA_SCHATTEN_INF = 0
+SEGSALSA_G4_AFFINE = 0
+SEGSALSA_G4_SIMPLEX = 1
 
 KERNEL_KINDS = ("sweep", "row_fft_forward", "column_solve", "row_fft_inverse", "diagnostics",
                 "other", "mlr")
@@ -40,7 +42,8 @@ SYMBOLS = (
     "segsalsa_str_batch_create", "segsalsa_str_batch_image", "segsalsa_str_batch_solve",
     "segsalsa_str_batch_autotune", "segsalsa_str_batch_set_lanes", "segsalsa_str_batch_get_lanes",
     "segsalsa_str_batch_destroy", "segsalsa_str_batch_last_error",
-    "segsalsa_str_set_spectra", "segsalsa_str_get_probs",
+    "segsalsa_str_set_spectra", "segsalsa_str_get_probs", "segsalsa_str_solve_until",
+    "segsalsa_str_set_g4",
 )
 
 
@@ -124,6 +127,9 @@ def load(path: str | None = None):
         "segsalsa_str_batch_destroy": (None, [vp]),
         "segsalsa_str_set_spectra": (C.c_int, [vp, vp, vp, vp, i32, i32]),
         "segsalsa_str_get_probs": (C.c_int, [vp, vp, i32, i32]),
+        "segsalsa_str_set_g4": (C.c_int, [vp, i32]),
+        "segsalsa_str_solve_until": (C.c_int, [vp, i32, C.c_double, C.c_double, i32,
+                                               C.POINTER(i32), C.POINTER(C.c_double)]),
         "segsalsa_str_batch_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -333,6 +339,21 @@ class Solver:
         ptr, dev = _ptr(out, self.dtype)
         self._c(self.lib.segsalsa_str_get_probs(self.h, ptr, layout, dev))
         return out
+
+    # segsalsa_str_set_g4
+    def set_g4(self, mode):
+        m = {"affine": SEGSALSA_G4_AFFINE, "simplex": SEGSALSA_G4_SIMPLEX}.get(mode, mode)
+        self._c(self.lib.segsalsa_str_set_g4(self.h, int(m)))
+
+    # segsalsa_str_solve_until
+    def solve_until(self, max_iters, tol_primal, tol_dual, check_every=10):
+        """Returns (iterations run, last trace record as a 6-vector)."""
+        n = C.c_int32(0)
+        rec = (C.c_double * 6)()
+        self._c(self.lib.segsalsa_str_solve_until(self.h, int(max_iters), float(tol_primal),
+                                                  float(tol_dual), int(check_every),
+                                                  C.byref(n), rec))
+        return n.value, np.array(rec[:], dtype=np.float64)
 
     # segsalsa_str_get_labels
     def get_labels(self, out=None):

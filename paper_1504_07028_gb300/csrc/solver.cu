@@ -66,6 +66,8 @@ struct SolverBase {
   virtual int enqueue_read_err(int* host, cudaStream_t s) = 0;   // copy the device error flag
   virtual int clear_err(cudaStream_t s) = 0;
   virtual void invalidate() = 0;                       // forget p and the iterates
+  virtual int set_g4(int mode) = 0;
+  virtual int generation() const = 0;                  // changes when launches change
   int fail(int code, const std::string& m) { err = m; return code; }
 };
 
@@ -366,6 +368,8 @@ class Solver : public SolverBase {
   size_t mlr_cap = 0;
   int trace_host_cap = 0;
   bool use_graphs = true;
+  int g4 = SEGSALSA_G4_AFFINE;   // MPO of g4: affine set (eq. 10) or probability simplex
+  int gen = 0;
 
   ~Solver() override {
     if (st) cudaStreamSynchronize(st);
@@ -545,7 +549,10 @@ class Solver : public SolverBase {
     a.tau = (T)(lambda / mu); a.mu = (T)mu; a.invK = (T)(1.0 / pl.K); a.sp = sp;
     a.err = b.err;
     const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
-    SGS_CUDA(launch(KIND_SWEEP, [&]() { return launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st); }));
+    SGS_CUDA(launch(KIND_SWEEP, [&]() {
+      return g4 == SEGSALSA_G4_SIMPLEX ? launch_sweep_simplex<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st)
+                                       : launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
+    }));
     return SEGSALSA_OK;
   }
 
@@ -974,6 +981,20 @@ class Solver : public SolverBase {
     return SEGSALSA_OK;
   }
   void invalidate() override { have_probs = false; iter = 0; rhs_dense = false; }
+  int generation() const override { return gen; }
+  int set_g4(int mode) override {
+    if (mode != SEGSALSA_G4_AFFINE && mode != SEGSALSA_G4_SIMPLEX) return fail(SEGSALSA_ERR_ARG, "bad g4 mode");
+    if (mode == g4) return SEGSALSA_OK;
+    if (mode == SEGSALSA_G4_SIMPLEX)
+      SGS_CUDA(prepare_sweep_simplex<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
+    SGS_CUDA(cudaStreamSynchronize(st));
+    for (auto& kv : chunks)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    chunks.clear();
+    g4 = mode;
+    ++gen;
+    return SEGSALSA_OK;
+  }
 
   int traffic(double* sw, double* it) const override {
     const double unit = (double)sizeof(T) * pl.n * pl.K;
@@ -1064,6 +1085,7 @@ struct segsalsa_str_batch {
   cudaEvent_t fork = nullptr;
   std::vector<std::vector<int>> lane_img;
   std::map<int, cudaGraphExec_t> graphs;     // by chunk length
+  std::vector<int> graph_gen;                // image generations the graphs were captured at
   int* err_host = nullptr;                   // pinned, one flag per image
 
   int fail(int code, const std::string& m) { err = m; return code; }
@@ -1189,6 +1211,13 @@ struct segsalsa_str_batch {
   }
 
   int get_graph(int len, cudaGraphExec_t& out) {
+    bool stale = (int)graph_gen.size() != n;
+    for (int i = 0; i < n && !stale; ++i) stale = graph_gen[i] != img[i]->impl->generation();
+    if (stale) {
+      drop_graphs();
+      graph_gen.resize(n);
+      for (int i = 0; i < n; ++i) graph_gen[i] = img[i]->impl->generation();
+    }
     auto it = graphs.find(len);
     if (it != graphs.end()) { out = it->second; return SEGSALSA_OK; }
     SGB_CUDA(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
@@ -1486,6 +1515,37 @@ int segsalsa_str_set_probs(segsalsa_str_t* h, const void* p, int32_t layout, int
 int segsalsa_str_solve(segsalsa_str_t* h, int32_t iters, double* trace, int32_t every, int32_t* nrec) {
   SGS_H(h); return h->impl->solve(iters, trace, every, nrec);
 }
+int segsalsa_str_solve_until(segsalsa_str_t* h, int32_t max_iters, double tol_primal,
+                             double tol_dual, int32_t check_every, int32_t* iters_done,
+                             double* last_record) {
+  SGS_H(h);
+  sgs::SolverBase& s = *h->impl;
+  if (max_iters < 0) return s.fail(SEGSALSA_ERR_ARG, "max_iters must be >= 0");
+  if (check_every < 1) return s.fail(SEGSALSA_ERR_ARG, "check_every must be >= 1");
+  if (!(tol_primal >= 0.0) || !(tol_dual >= 0.0) || !std::isfinite(tol_primal) ||
+      !std::isfinite(tol_dual))
+    return s.fail(SEGSALSA_ERR_ARG, "tolerances must be finite and >= 0");
+  int done = 0;
+  double rec[12] = {0};
+  double last[6] = {0};
+  bool have = false;
+  while (done < max_iters) {
+    const int len = std::min(check_every, max_iters - done);
+    int n = 0;
+    const int rc = s.solve(len, rec, len, &n);
+    if (rc) return rc;
+    done += len;
+    if (n > 0) {
+      for (int j = 0; j < 6; ++j) last[j] = rec[6 * (n - 1) + j];
+      have = true;
+      if (last[1] <= tol_primal && last[2] <= tol_dual) break;
+    }
+  }
+  if (iters_done) *iters_done = done;
+  if (last_record)
+    for (int j = 0; j < 6; ++j) last_record[j] = have ? last[j] : std::nan("");
+  return SEGSALSA_OK;
+}
 int segsalsa_str_get_labels(segsalsa_str_t* h, int32_t* lab, int32_t dev) {
   SGS_H(h); return h->impl->get_labels(lab, dev);
 }
@@ -1512,6 +1572,9 @@ int segsalsa_str_set_spectra(segsalsa_str_t* h, const void* x, const void* w, co
 }
 int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t dev) {
   SGS_H(h); return h->impl->get_probs(p, layout, dev);
+}
+int segsalsa_str_set_g4(segsalsa_str_t* h, int32_t mode) {
+  SGS_H(h); return h->impl->set_g4(mode);
 }
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on) {
   SGS_H(h); return h->impl->set_profiling(on);

@@ -182,7 +182,9 @@ __device__ __forceinline__ void flush_row(const T (&w)[E], const T (&w2)[DIAG ? 
 template <typename T, int M, bool DIAG>
 constexpr int sweep_min_blocks() { return (sizeof(T) == 8 || M >= 2 || DIAG) ? 2 : 3; }
 
-template <typename T, int M, int G, bool DIAG>
+// SIMP selects the MPO of g4: false, the projection onto the affine set 1^T xi = 1 (eq. 10);
+// true, the projection onto the probability simplex (Sec. 4's description of that MPO).
+template <typename T, int M, int G, bool DIAG, bool SIMP>
 __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(const SweepArgs<T> a) {
   constexpr int L = (2 * M + 1) * (2 * M + 1);
   constexpr int E = 2 * M + 2;
@@ -386,7 +388,27 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     const T sroot = (pv >= T(0)) ? T(0.5) * (pv + disc) : (T(0.5) * q) / (disc - pv);
     const T u1 = v1 + pk / (mu * sroot);
     const T u3 = fmax(v3, T(0));
-    const T u4 = v4 - (s4 - T(1)) * a.invK;
+    T u4;
+    if constexpr (!SIMP) {
+      u4 = v4 - (s4 - T(1)) * a.invK;
+    } else {
+      // Michelot: threshold over the active classes until no class leaves the active set (at
+      // most K passes; the loop runs until no group of the warp changes, so that every lane
+      // takes part in the shuffles)
+      (void)s4;
+      bool act = kok;
+      T theta = T(0);
+      for (int pass = 0; pass < 32; ++pass) {
+        const T cnt = group_sum<G>(act ? T(1) : T(0));
+        const T sum = group_sum<G>(act ? v4 : T(0));
+        theta = (cnt > T(0)) ? (sum - T(1)) / cnt : T(0);
+        const bool nact = act && (v4 > theta);
+        const bool changed = nact != act;
+        act = nact;
+        if (!__any_sync(0xffffffffu, changed)) break;
+      }
+      u4 = kok ? fmax(v4 - theta, T(0)) : T(0);
+    }
     const T n1 = u1 - v1, n3 = u3 - v3, n4 = u4 - v4;
     if (kok) {
       T* dl = a.dloc + pix * 3 * K + g;
@@ -432,57 +454,76 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
 }
 
 // Largest dynamic shared memory granted so far to each sweep variant.
-template <typename T, int M, int G, bool DIAG>
+template <typename T, int M, int G, bool DIAG, bool SIMP>
 struct SweepGrant {
   static size_t v;
 };
-template <typename T, int M, int G, bool DIAG> size_t SweepGrant<T, M, G, DIAG>::v = 0;
+template <typename T, int M, int G, bool DIAG, bool SIMP>
+size_t SweepGrant<T, M, G, DIAG, SIMP>::v = 0;
 
-template <typename T, int M, int G, bool DIAG>
+template <typename T, int M, int G, bool DIAG, bool SIMP>
 inline cudaError_t grant_sweep(size_t smem) {
-  size_t& g = SweepGrant<T, M, G, DIAG>::v;
+  size_t& g = SweepGrant<T, M, G, DIAG, SIMP>::v;
   if (smem <= g) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG>,
+  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG, SIMP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) g = smem;
   return e;
 }
 
-template <typename T, int M, int G, bool DIAG>
+template <typename T, int M, int G, bool DIAG, bool SIMP>
 inline cudaError_t launch_sweep_inst(const SweepArgs<T>& a, int tiles, size_t smem,
                                      cudaStream_t st) {
-  cudaError_t e = grant_sweep<T, M, G, DIAG>(smem);
+  cudaError_t e = grant_sweep<T, M, G, DIAG, SIMP>(smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_sweep<T, M, G, DIAG>, dim3(tiles), dim3(256), smem, st, a);
+  return launch_pdl(k_sweep<T, M, G, DIAG, SIMP>, dim3(tiles), dim3(256), smem, st, a);
 }
 
-template <typename T, int M, int G>
+template <typename T, int M, int G, bool SIMP>
 inline cudaError_t prepare_sweep_inst(size_t smem, size_t smem_diag) {
-  cudaError_t e = grant_sweep<T, M, G, false>(smem);
+  cudaError_t e = grant_sweep<T, M, G, false, SIMP>(smem);
   if (e != cudaSuccess) return e;
-  return grant_sweep<T, M, G, true>(smem_diag);
+  return grant_sweep<T, M, G, true, SIMP>(smem_diag);
 }
 
-template <typename T, int M, bool DIAG>
+template <typename T, int M, bool DIAG, bool SIMP>
 inline cudaError_t launch_sweep_g(const SweepArgs<T>& a, int G, int tiles, size_t smem,
                                   cudaStream_t st) {
   switch (G) {
-    case 4: return launch_sweep_inst<T, M, 4, DIAG>(a, tiles, smem, st);
-    case 8: return launch_sweep_inst<T, M, 8, DIAG>(a, tiles, smem, st);
-    case 16: return launch_sweep_inst<T, M, 16, DIAG>(a, tiles, smem, st);
-    case 32: return launch_sweep_inst<T, M, 32, DIAG>(a, tiles, smem, st);
+    case 4: return launch_sweep_inst<T, M, 4, DIAG, SIMP>(a, tiles, smem, st);
+    case 8: return launch_sweep_inst<T, M, 8, DIAG, SIMP>(a, tiles, smem, st);
+    case 16: return launch_sweep_inst<T, M, 16, DIAG, SIMP>(a, tiles, smem, st);
+    case 32: return launch_sweep_inst<T, M, 32, DIAG, SIMP>(a, tiles, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T, bool DIAG>
+template <typename T, bool DIAG, bool SIMP>
 inline cudaError_t launch_sweep_md(const SweepArgs<T>& a, int M, int G, int tiles, size_t smem,
                                    cudaStream_t st) {
   switch (M) {
-    case 0: return launch_sweep_g<T, 0, DIAG>(a, G, tiles, smem, st);
-    case 1: return launch_sweep_g<T, 1, DIAG>(a, G, tiles, smem, st);
-    case 2: return launch_sweep_g<T, 2, DIAG>(a, G, tiles, smem, st);
+    case 0: return launch_sweep_g<T, 0, DIAG, SIMP>(a, G, tiles, smem, st);
+    case 1: return launch_sweep_g<T, 1, DIAG, SIMP>(a, G, tiles, smem, st);
+    case 2: return launch_sweep_g<T, 2, DIAG, SIMP>(a, G, tiles, smem, st);
   }
+  return cudaErrorInvalidValue;
+}
+
+// The instantiations of one precision and one g4 variant (each in its own translation unit).
+template <typename T, bool SIMP>
+inline cudaError_t launch_sweep_variant(const SweepArgs<T>& a, int M, int G, bool diag,
+                                        int tiles, size_t smem, cudaStream_t st) {
+  return diag ? launch_sweep_md<T, true, SIMP>(a, M, G, tiles, smem, st)
+              : launch_sweep_md<T, false, SIMP>(a, M, G, tiles, smem, st);
+}
+template <typename T, bool SIMP>
+inline cudaError_t prepare_sweep_variant(int M, int G, size_t smem, size_t smem_diag) {
+#define SGS_PREP(MM, GG) \
+  if (M == MM && G == GG) return prepare_sweep_inst<T, MM, GG, SIMP>(smem, smem_diag);
+  SGS_PREP(0, 4) SGS_PREP(0, 8) SGS_PREP(0, 16) SGS_PREP(0, 32)
+  SGS_PREP(1, 4) SGS_PREP(1, 8) SGS_PREP(1, 16) SGS_PREP(1, 32)
+  SGS_PREP(2, 4) SGS_PREP(2, 8) SGS_PREP(2, 16) SGS_PREP(2, 32)
+#undef SGS_PREP
   return cudaErrorInvalidValue;
 }
 

@@ -8,7 +8,7 @@ import tests.test_oracle_pins as P
 
 _orig = {name: getattr(O, name) for name in
          ("shift", "prox_g1", "prox_g2", "linear_solve", "prox_g4", "D_v_T", "jacobian",
-          "mlr_probs")}
+          "mlr_probs", "proj_simplex")}
 
 
 def _wrong_shift(f, s):                     # shift sign flipped
@@ -59,6 +59,10 @@ def _wrong_softmax_axis(x, Wc, b=None):     # normalised over pixels instead of 
     return np.ascontiguousarray((e / e.sum(axis=0, keepdims=True)).T.reshape(-1, H, W))
 
 
+def _wrong_affine_for_simplex(v):           # the affine projection where the simplex one belongs
+    return v - (np.sum(v, axis=0, keepdims=True) - 1.0) / v.shape[0]
+
+
 MUTATIONS = [
     ("shift", _wrong_shift, [P.test_jacobian_brute_force_loops]),
     ("prox_g1", _wrong_root, [P.test_prox_g1_stationarity]),
@@ -71,6 +75,7 @@ MUTATIONS = [
     ("jacobian", _dropped_weight, [lambda: P.test_JTJ_equals_weighted_laplacian(1),
                                    lambda: P.test_symbol_closed_form(6, 8, 1)]),
     ("mlr_probs", _dropped_bias, [P.test_mlr_brute_force]),
+    ("proj_simplex", _wrong_affine_for_simplex, [P.test_simplex_g4_variant_u4_on_simplex]),
     ("mlr_probs", _wrong_softmax_axis, [P.test_mlr_brute_force, P.test_mlr_special_cases]),
 ]
 

@@ -391,3 +391,29 @@ def test_mlr_scene_margin():
     other = np.where(np.eye(9, dtype=bool)[y], -np.inf, lg).max(axis=-1)
     assert 0.5 < np.median(true - other) < 4.0
     assert np.mean(np.argmax(lg, axis=-1) == y) > 0.6
+
+
+# ------------------------------------------- g4 read as the simplex indicator (variant)
+
+def test_simplex_g4_variant_same_minimum():
+    """Sec. 4 describes the MPO of g4 as the projection onto the probability simplex while
+    eq. (10) defines g4 on the affine set; with g3 = i_+ present both splittings constrain z to
+    the same simplex, so the convex problem (7) has the same minimum value either way."""
+    sc = synth.scene(10, 10, 3, S=3, gap=1.5, noise_std=1.0, wrong_frac=0.0, seed=44)
+    om = O.gaussian_weights(1, 0.5)
+    sa, _ = O.solve(sc.p, 1, 0.5, 0.8, 1.0, 1, 2500)
+    ss, _ = O.solve(sc.p, 1, 0.5, 0.8, 1.0, 1, 2500, g4="simplex")
+    fa = O.objective(O.proj_simplex(sa.z), sc.p, 0.8, om, 1, 1)
+    fs = O.objective(O.proj_simplex(ss.z), sc.p, 0.8, om, 1, 1)
+    assert abs(fa - fs) < 1e-6 * abs(fa)
+    assert np.abs(sa.z - ss.z).max() > 1e-12          # the iterates themselves differ
+
+
+def test_simplex_g4_variant_u4_on_simplex():
+    sc = synth.scene(8, 9, 4, S=3, gap=1.0, noise_std=2.0, wrong_frac=0.2, seed=45)
+    om = O.gaussian_weights(1, 0.5)
+    st, _ = O.solve(sc.p, 1, 0.5, 1.5, 1.0, 2, 2, g4="simplex")
+    u4 = st.u[3]
+    assert u4.min() >= 0.0 and np.abs(u4.sum(axis=0) - 1.0).max() < 1e-12
+    sa, _ = O.solve(sc.p, 1, 0.5, 1.5, 1.0, 2, 2)
+    assert sa.u[3].min() < 0.0                        # the affine variant leaves the orthant
