@@ -131,6 +131,38 @@ int segsalsa_str_solve_until(segsalsa_str_t* h, int32_t max_iters, double tol_pr
  * kept. SEGSALSA_ERR_ARG for another mode. */
 int segsalsa_str_set_g4(segsalsa_str_t* h, int32_t mode);
 
+/* ------------------------------------------------------------------------------------------
+ * Differentiable solver: the gradient of the unrolled iteration (12)-(14).
+ * ------------------------------------------------------------------------------------------ */
+
+/* Like set_probs, from log-probabilities: p_i = exp(log p_i - max_k log p_ik) (the iterates do
+ * not see a per-pixel scale of p). H*W*K values in `layout`, handle precision. */
+int segsalsa_str_set_log_probs(segsalsa_str_t* h, const void* log_p, int32_t layout,
+                               int32_t on_device);
+
+/* Change lambda of eq. (7) (finite, >= 0) or the L shift weights omega_j of eq. (4) (host,
+ * finite) of an existing handle; the state is kept and the change applies from the next
+ * iteration. SEGSALSA_ERR_ARG for invalid values. */
+int segsalsa_str_set_lambda(segsalsa_str_t* h, double lambda);
+int segsalsa_str_set_weights(segsalsa_str_t* h, const double* weights);
+
+/* Reverse pass. With z^T the field after `iters` >= 1 iterations started from the current p
+ * (z^0 = p_i / 1^T p_i, u^0 = G z^0, d^0 = 0) and zbar = dLoss/dz^T (H*W*K values in `layout`),
+ * writes dLoss/dlog p (same shape and layout; required), dLoss/dlambda (nullable, host) and
+ * dLoss/domega_j (nullable, host, L values). The call runs the forward pass itself, keeping a
+ * checkpoint of the state every `checkpoint_every` >= 1 iterations, then walks the iterations
+ * backwards, recomputing each segment's states from its checkpoint: the adjoint of the z-update
+ * is the z-update itself (G^T G is symmetric), the adjoints of the MPOs of g1..g4 are their
+ * Jacobians applied per pixel, and the adjoint of J is J^T. Device memory for the checkpoints
+ * and one segment's states is allocated for the call and released before it returns. The
+ * handle ends at iteration `iters`, as after set_probs + solve(iters).
+ * Covers Schatten p = 1 and 2 with g4 on the affine set; SEGSALSA_ERR_ARG otherwise. The
+ * derivative is that of the iteration as written: at points where an MPO switches case (a
+ * singular value equal to tau, a component of v3 equal to 0) one side's derivative is taken. */
+int segsalsa_str_backward(segsalsa_str_t* h, int32_t iters, const void* zbar, int32_t layout,
+                          void* grad_logp, double* grad_lambda, double* grad_weights,
+                          int32_t checkpoint_every, int32_t on_device);
+
 /* Label readout argmax_k z_k of every pixel (link p(y_i = k | z_i) = [z_i]_k, Sec. 2; ties to
  * the lowest k), H*W int32 in row-major pixel order. */
 int segsalsa_str_get_labels(segsalsa_str_t* h, int32_t* labels, int32_t on_device);

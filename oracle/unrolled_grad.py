@@ -131,5 +131,6 @@ def reference_gradient(log_p, lam, omega, M, mu, sp, iters, zbar):
     om = torch.tensor(np.asarray(omega, dtype=np.float64), requires_grad=True)
     z = unrolled(lp, la, om, M, mu, sp, iters)
     loss = torch.sum(torch.tensor(np.asarray(zbar, dtype=np.float64)) * z)
-    g = torch.autograd.grad(loss, (lp, la, om))
+    g = torch.autograd.grad(loss, (lp, la, om), allow_unused=True)   # z^1 does not see lambda
+    g = [torch.zeros_like(x) if gi is None else gi for gi, x in zip(g, (lp, la, om))]
     return (g[0].numpy(), float(g[1]), g[2].numpy(), z.detach().numpy())

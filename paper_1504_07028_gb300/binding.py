@@ -43,7 +43,8 @@ SYMBOLS = (
     "segsalsa_str_batch_autotune", "segsalsa_str_batch_set_lanes", "segsalsa_str_batch_get_lanes",
     "segsalsa_str_batch_destroy", "segsalsa_str_batch_last_error",
     "segsalsa_str_set_spectra", "segsalsa_str_get_probs", "segsalsa_str_solve_until",
-    "segsalsa_str_set_g4",
+    "segsalsa_str_set_g4", "segsalsa_str_set_log_probs", "segsalsa_str_set_lambda",
+    "segsalsa_str_set_weights", "segsalsa_str_backward",
 )
 
 
@@ -128,6 +129,11 @@ def load(path: str | None = None):
         "segsalsa_str_set_spectra": (C.c_int, [vp, vp, vp, vp, i32, i32]),
         "segsalsa_str_get_probs": (C.c_int, [vp, vp, i32, i32]),
         "segsalsa_str_set_g4": (C.c_int, [vp, i32]),
+        "segsalsa_str_set_log_probs": (C.c_int, [vp, vp, i32, i32]),
+        "segsalsa_str_set_lambda": (C.c_int, [vp, C.c_double]),
+        "segsalsa_str_set_weights": (C.c_int, [vp, C.POINTER(C.c_double)]),
+        "segsalsa_str_backward": (C.c_int, [vp, i32, vp, i32, vp, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), i32, i32]),
         "segsalsa_str_solve_until": (C.c_int, [vp, i32, C.c_double, C.c_double, i32,
                                                C.POINTER(i32), C.POINTER(C.c_double)]),
         "segsalsa_str_batch_last_error": (C.c_char_p, [vp]),
@@ -339,6 +345,37 @@ class Solver:
         ptr, dev = _ptr(out, self.dtype)
         self._c(self.lib.segsalsa_str_get_probs(self.h, ptr, layout, dev))
         return out
+
+    # segsalsa_str_set_log_probs
+    def set_log_probs(self, log_p, layout=SEGSALSA_LAYOUT_KHW):
+        ptr, dev = _ptr(log_p, self.dtype)
+        self._c(self.lib.segsalsa_str_set_log_probs(self.h, ptr, layout, dev))
+
+    # segsalsa_str_set_lambda
+    def set_lambda(self, lam):
+        self._c(self.lib.segsalsa_str_set_lambda(self.h, float(lam)))
+
+    # segsalsa_str_set_weights
+    def set_weights(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.shape != (self.L,):
+            raise ValueError(f"weights must have {self.L} entries")
+        self._c(self.lib.segsalsa_str_set_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_double))))
+
+    # segsalsa_str_backward
+    def backward(self, iters, zbar, checkpoint_every=10, out=None, layout=SEGSALSA_LAYOUT_KHW):
+        """Returns (dLoss/dlog p, dLoss/dlambda, dLoss/domega) for zbar = dLoss/dz^T."""
+        if out is None:
+            out = np.empty_like(zbar) if isinstance(zbar, np.ndarray) else zbar.new_empty(zbar.shape)
+        p1, d1 = _ptr(zbar, self.dtype)
+        p2, d2 = _ptr(out, self.dtype)
+        if d1 != d2:
+            raise ValueError("zbar and the output must both be host or both device arrays")
+        glam = C.c_double(0)
+        gom = (C.c_double * self.L)()
+        self._c(self.lib.segsalsa_str_backward(self.h, int(iters), p1, layout, p2, C.byref(glam),
+                                               gom, int(checkpoint_every), d1))
+        return out, glam.value, np.array(gom[:], dtype=np.float64)
 
     # segsalsa_str_set_g4
     def set_g4(self, mode):

@@ -25,6 +25,7 @@
 #include "fft.cuh"
 #include "launch.h"
 #include "mlr.cuh"
+#include "adjoint.cuh"
 
 namespace sgs {
 
@@ -67,6 +68,11 @@ struct SolverBase {
   virtual int clear_err(cudaStream_t s) = 0;
   virtual void invalidate() = 0;                       // forget p and the iterates
   virtual int set_g4(int mode) = 0;
+  virtual int set_log_probs(const void* logp, int layout, int dev) = 0;
+  virtual int set_lambda(double lam) = 0;
+  virtual int set_weights(const double* w) = 0;
+  virtual int backward(int iters, const void* zbar, int layout, void* glogp, double* glam,
+                       double* gom, int every, int dev) = 0;
   virtual int generation() const = 0;                  // changes when launches change
   int fail(int code, const std::string& m) { err = m; return code; }
 };
@@ -996,6 +1002,209 @@ class Solver : public SolverBase {
     return SEGSALSA_OK;
   }
 
+  void drop_chunks() {
+    for (auto& kv : chunks)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    chunks.clear();
+    ++gen;
+  }
+
+  int set_log_probs(const void* logp, int layout, int dev) override {
+    if (!logp) return fail(SEGSALSA_ERR_ARG, "log p is NULL");
+    if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
+    const size_t nK = (size_t)pl.n * pl.K;
+    int rc;
+    T* src = b.zp;
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_in(b.zp, logp, nK, dev))) return rc;
+    } else {
+      if ((rc = copy_in(b.tmp, logp, nK, dev))) return rc;
+      SGS_LAUNCH(KIND_OTHER, (k_khw_to_hwk<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.tmp, b.zp, pl.n, pl.K)));
+    }
+    const AdjShape sh{pl.H, pl.W, pl.K, pl.n};
+    SGS_LAUNCH(KIND_OTHER, launch_exp_logp<T>(sh, pl.G, src, b.tmp, st));
+    return commit_probs();
+  }
+
+  int set_lambda(double lam) override {
+    if (!(lam >= 0.0) || !std::isfinite(lam)) return fail(SEGSALSA_ERR_ARG, "lambda must be finite and >= 0");
+    SGS_CUDA(cudaStreamSynchronize(st));
+    lambda = lam;
+    drop_chunks();
+    return SEGSALSA_OK;
+  }
+
+  int set_weights(const double* w) override {
+    if (!w) return fail(SEGSALSA_ERR_ARG, "weights is NULL");
+    for (int j = 0; j < pl.L; ++j)
+      if (!std::isfinite(w[j])) return fail(SEGSALSA_ERR_ARG, "weights must be finite");
+    SGS_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < pl.L; ++j) omega[j] = w[j];
+    c_omega = 0.0;
+    for (double v : omega) c_omega += v * v;
+    drop_chunks();
+    return upload_tables();
+  }
+
+  // Reverse pass of `iters` iterations from the current p (see adjoint.cuh for the algebra).
+  int backward(int iters, const void* zbar, int layout, void* glogp, double* glam, double* gom,
+               int every, int dev) override {
+    if (!have_probs) return fail(SEGSALSA_ERR_STATE, "backward before set_probs");
+    if (iters < 1) return fail(SEGSALSA_ERR_ARG, "iters must be >= 1");
+    if (every < 1) return fail(SEGSALSA_ERR_ARG, "checkpoint_every must be >= 1");
+    if (!zbar || !glogp) return fail(SEGSALSA_ERR_ARG, "zbar and grad_logp are required");
+    if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
+    if (sp == 0) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers Schatten p = 1 and 2");
+    if (g4 != SEGSALSA_G4_AFFINE) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers g4 on the affine set");
+    const int K = pl.K, L = pl.L, n = pl.n;
+    const size_t nK = (size_t)n * K, nloc = 3 * nK, n2 = 2 * (size_t)L * nK;
+    const size_t tslot = (size_t)pl.ntiles * pl.EHmax * pl.EWmax * K;
+    const size_t st_elems = nK + nloc + n2 + tslot;          // z, d1/d3/d4, d2, rhs partials
+    const int nseg = (iters + every - 1) / every;
+    const int blocks = (n + ADJ_THREADS / pl.G - 1) / (ADJ_THREADS / pl.G);
+    const size_t npart = (size_t)blocks * (L + 2);
+    // device memory of the pass (released at the end)
+    Carver cv{nullptr};
+    auto plan = [&](Carver& c, T*& ck, T*& fin, T*& zs, T*& dls, T*& d2s, T*& vb, T*& zb, T*& bb,
+                    T*& glp, double*& part) {
+      ck = c.take<T>((size_t)nseg * st_elems);
+      fin = c.take<T>(st_elems);
+      zs = c.take<T>((size_t)(every + 2) * nK);
+      dls = c.take<T>((size_t)(every + 1) * nloc);
+      d2s = c.take<T>((size_t)(every + 1) * n2);
+      vb = c.take<T>(2 * (nloc + n2));
+      zb = c.take<T>(nK);
+      bb = c.take<T>(nK);
+      glp = c.take<T>(nK);
+      part = c.take<double>(npart);
+    };
+    T *ck, *fin, *zs, *dls, *d2s, *vb, *zb, *bb, *glp;
+    double* part;
+    plan(cv, ck, fin, zs, dls, d2s, vb, zb, bb, glp, part);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, cv.off);
+    if (e != cudaSuccess) return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    struct Free { void* m; ~Free() { cudaFree(m); } } guard{mem};
+    Carver cm{static_cast<char*>(mem)};
+    plan(cm, ck, fin, zs, dls, d2s, vb, zb, bb, glp, part);
+    auto save = [&](T* dst) -> cudaError_t {
+      cudaError_t r;
+      if ((r = cudaMemcpyAsync(dst, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st))) return r;
+      if ((r = cudaMemcpyAsync(dst + nK, b.dloc, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st))) return r;
+      if ((r = cudaMemcpyAsync(dst + nK + nloc, b.d2, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st))) return r;
+      return cudaMemcpyAsync(dst + nK + nloc + n2, b.P, sizeof(T) * tslot, cudaMemcpyDeviceToDevice, st);
+    };
+    auto load = [&](const T* src) -> cudaError_t {
+      cudaError_t r;
+      if ((r = cudaMemcpyAsync(b.z, src, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st))) return r;
+      if ((r = cudaMemcpyAsync(b.dloc, src + nK, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st))) return r;
+      if ((r = cudaMemcpyAsync(b.d2, src + nK + nloc, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st))) return r;
+      return cudaMemcpyAsync(b.P, src + nK + nloc + n2, sizeof(T) * tslot, cudaMemcpyDeviceToDevice, st);
+    };
+    int rc;
+    // forward from z^0 = p / 1^T p, d^0 = 0, with a checkpoint every `every` iterations
+    SGS_LAUNCH(KIND_OTHER, (k_init_z<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.p, b.z, n, K)));
+    SGS_CUDA(cudaMemsetAsync(b.dloc, 0, sizeof(T) * nloc, st));
+    SGS_CUDA(cudaMemsetAsync(b.d2, 0, sizeof(T) * n2, st));
+    iter = 0;
+    rhs_dense = false;
+    for (int k = 0; k < iters; k += every) {
+      SGS_CUDA(save(ck + (size_t)(k / every) * st_elems));
+      if ((rc = solve(std::min(every, iters - k), nullptr, 0, nullptr))) return rc;
+    }
+    SGS_CUDA(save(fin));
+    // seed: zbar^T, pixel-major
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_in(zb, zbar, nK, dev))) return rc;
+    } else {
+      if ((rc = copy_in(b.tmp, zbar, nK, dev))) return rc;
+      SGS_LAUNCH(KIND_OTHER, (k_khw_to_hwk<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.tmp, zb, n, K)));
+    }
+    SGS_CUDA(cudaMemsetAsync(glp, 0, sizeof(T) * nK, st));
+    std::vector<double> hp(npart);
+    double tau_bar = 0.0, s_bar = 0.0;
+    std::vector<double> om_bar(L, 0.0);
+    const AdjShape sh{pl.H, pl.W, K, n};
+    bool first = true;
+    int cur = 0;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int k0 = seg * every;
+      const int k1 = std::min(k0 + every, iters - 1);
+      if (k1 < k0 + 1) continue;                              // no unit in this segment
+      // recompute z^k, d^k (k0 <= k <= k1) and z^{k1+1} from the checkpoint
+      SGS_CUDA(load(ck + (size_t)seg * st_elems));
+      iter = k0;
+      rhs_dense = false;
+      for (int k = k0; k <= k1; ++k) {
+        const int i = k - k0;
+        SGS_CUDA(cudaMemcpyAsync(zs + (size_t)i * nK, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st));
+        SGS_CUDA(cudaMemcpyAsync(dls + (size_t)i * nloc, b.dloc, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st));
+        SGS_CUDA(cudaMemcpyAsync(d2s + (size_t)i * n2, b.d2, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st));
+        if (k < k1) {
+          if ((rc = iteration(false, 0))) return rc;
+        } else {
+          if ((rc = z_update(nullptr, b.z))) return rc;         // z^{k1+1} (k1 >= 1)
+          SGS_CUDA(cudaMemcpyAsync(zs + (size_t)(i + 1) * nK, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st));
+        }
+      }
+      // reverse units k1 .. k0+1
+      for (int k = k1; k >= k0 + 1; --k) {
+        const int i = k - k0;
+        if ((rc = z_update(zb, bb))) return rc;                 // bbar = A^{-1} zbar^{k+1}
+        AdjArgs<T> a{};
+        a.s = sh;
+        a.zk = zs + (size_t)i * nK;
+        a.zk1 = zs + (size_t)(i + 1) * nK;
+        a.p = b.p;
+        a.dloc = dls + (size_t)(i - 1) * nloc;
+        a.d2 = d2s + (size_t)(i - 1) * n2;
+        a.bbar = bb;
+        T* vcur = vb + (size_t)cur * (nloc + n2);
+        T* vprev = vb + (size_t)(cur ^ 1) * (nloc + n2);
+        a.vn_loc = first ? nullptr : vprev;
+        a.vn_2 = first ? nullptr : vprev + nloc;
+        a.v_loc = vcur;
+        a.v_2 = vcur + nloc;
+        a.glogp = glp;
+        a.part = part;
+        a.omega = b.omega;
+        a.tau = (T)(lambda / mu);
+        a.mu = (T)mu;
+        a.invK = (T)(1.0 / K);
+        a.sp = sp;
+        SGS_LAUNCH(KIND_OTHER, launch_adj_vjp<T>(a, pl.M, pl.G, blocks, st));
+        SGS_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * npart, cudaMemcpyDeviceToHost, st));
+        SGS_LAUNCH(KIND_OTHER, launch_adj_gt<T>(sh, pl.M, vcur, vcur + nloc, b.omega, zb, st));
+        SGS_CUDA(cudaStreamSynchronize(st));
+        for (int bl = 0; bl < blocks; ++bl) {                   // fixed order: deterministic sums
+          const double* q = hp.data() + (size_t)bl * (L + 2);
+          tau_bar += q[0];
+          for (int j = 0; j < L; ++j) om_bar[j] += q[1 + j];
+          s_bar += q[L + 1];
+        }
+        first = false;
+        cur ^= 1;
+      }
+    }
+    // z^1 = z^0 = p / 1^T p: the rest of zbar flows into log p
+    SGS_LAUNCH(KIND_OTHER, launch_adj_init<T>(sh, pl.G, b.p, zb, glp, st));
+    if (layout == SEGSALSA_LAYOUT_HWK) {
+      if ((rc = copy_out(glogp, glp, nK, dev))) return rc;
+    } else {
+      SGS_LAUNCH(KIND_OTHER, (k_hwk_to_khw<T><<<grid1(nK), AUX_THREADS, 0, st>>>(glp, b.tmp, n, K)));
+      if ((rc = copy_out(glogp, b.tmp, nK, dev))) return rc;
+    }
+    // the handle ends where the forward pass ended: iteration `iters`
+    SGS_CUDA(load(fin));
+    iter = iters;
+    rhs_dense = false;
+    SGS_CUDA(cudaStreamSynchronize(st));
+    if (glam) *glam = tau_bar / mu;
+    if (gom)
+      for (int j = 0; j < L; ++j) gom[j] = om_bar[j] - 2.0 * omega[j] * s_bar;
+    return SEGSALSA_OK;
+  }
+
   int traffic(double* sw, double* it) const override {
     const double unit = (double)sizeof(T) * pl.n * pl.K;
     if (sw) *sw = unit * (4.0 * pl.L + 9.0);
@@ -1575,6 +1784,22 @@ int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t d
 }
 int segsalsa_str_set_g4(segsalsa_str_t* h, int32_t mode) {
   SGS_H(h); return h->impl->set_g4(mode);
+}
+int segsalsa_str_set_log_probs(segsalsa_str_t* h, const void* logp, int32_t layout, int32_t dev) {
+  SGS_H(h); return h->impl->set_log_probs(logp, layout, dev);
+}
+int segsalsa_str_set_lambda(segsalsa_str_t* h, double lambda) {
+  SGS_H(h); return h->impl->set_lambda(lambda);
+}
+int segsalsa_str_set_weights(segsalsa_str_t* h, const double* weights) {
+  SGS_H(h); return h->impl->set_weights(weights);
+}
+int segsalsa_str_backward(segsalsa_str_t* h, int32_t iters, const void* zbar, int32_t layout,
+                          void* grad_logp, double* grad_lambda, double* grad_weights,
+                          int32_t checkpoint_every, int32_t dev) {
+  SGS_H(h);
+  return h->impl->backward(iters, zbar, layout, grad_logp, grad_lambda, grad_weights,
+                           checkpoint_every, dev);
 }
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on) {
   SGS_H(h); return h->impl->set_profiling(on);
