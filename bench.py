@@ -280,6 +280,9 @@ def run_reference(args, rank, world):
     if args.workload == "mlr610x340":
         run_reference_mlr(args)
         return
+    if args.workload == "diff256":
+        run_reference_diff(args)
+        return
     sc, cfgs, desc = make_workload(args.workload)
     per_p = max(1, args.ref_iters)
     for _ in range(args.warmup):
@@ -837,6 +840,202 @@ def run_mlr(args, rank, world, local_rank):
     s.close()
 
 
+DIFF_DESC = ("256x256 K=8, 3x3 Gaussian patch sigma=0.5, lambda=2, mu=1, Schatten p=1: gradient of "
+             "<zbar, z^50> with respect to log p, lambda and the 9 shift weights (forward pass, "
+             "checkpoints every 10 iterations, reverse pass)")
+
+
+def oracle_grad_sample():
+    """FP64 reference gradient (oracle autograd) on a 64x64 crop of the differentiable
+    workload; returns (full-image differentiated iterations per second, wall s, cores)."""
+    from oracle import segsalsa_str_oracle as O
+    from oracle import unrolled_grad as U
+    from paper_1504_07028_gb300 import synth
+    sc = synth.scene_256x256_k8()
+    cfg = synth.CFG_256
+    lp = np.log(sc.p[:, :64, :64])
+    zb = np.random.default_rng(7).normal(size=lp.shape)
+    t0, c0 = time.perf_counter(), time.process_time()
+    U.reference_gradient(lp, cfg.lam, O.gaussian_weights(cfg.M, cfg.sigma), cfg.M, cfg.mu,
+                         cfg.schatten_p, cfg.iters, zb)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return cfg.iters * (64 * 64) / (256 * 256) / wall, wall, max(1, round(cpu / wall))
+
+
+def run_diff(args, rank, world, local_rank):
+    """Differentiable solver. One step = set_log_probs (device log p) + segsalsa_str_backward
+    (forward pass with checkpoints, reverse pass) giving d/dlog p on the device and d/dlambda,
+    d/domega on the host. value = differentiated ADMM iterations per second."""
+    import torch
+    from paper_1504_07028_gb300 import binding as B
+    from paper_1504_07028_gb300 import build as Bu
+    from paper_1504_07028_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    Bu.build()
+    sc = synth.scene_256x256_k8()
+    cfg = synth.CFG_256
+    H, W, K = sc.H, sc.W, sc.K
+    mk = lambda prec: B.Solver(B.make_params(H, W, K, M=cfg.M, sigma=cfg.sigma, lam=cfg.lam,
+                                             mu=cfg.mu, schatten_p=cfg.schatten_p, precision=prec))
+    s = mk("fp32")
+    lp = torch.tensor(np.log(sc.p), dtype=torch.float32, device=dev)
+    zb = torch.tensor(np.random.default_rng(7).normal(size=(K, H, W)), dtype=torch.float32,
+                      device=dev)
+    g = torch.empty_like(lp)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    every = 10
+
+    def step(lp_in, zb_in, out):
+        s.set_log_probs(lp_in)
+        return s.backward(cfg.iters, zb_in, every, out=out)
+
+    for _ in range(args.warmup):
+        step(lp, zb, g)
+    torch.cuda.synchronize()
+    s.reset_stats()
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = step(lp, zb, g)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_ms = max_over_ranks(float(sum(times)), dev)
+    launches = sum(c for c, _ in s.kernel_stats().values())
+    value = whole_job_rate(cfg.iters * args.steps, world, total_ms * 1e-3)
+    # forward alone, for the cost of differentiation
+    t_fwd = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.set_log_probs(lp)
+        s.solve(cfg.iters)
+        b.record(stream)
+        b.synchronize()
+        t_fwd.append(a.elapsed_time(b))
+    # per-kernel device times (profiled eager replay of one step)
+    s.reset_stats()
+    s.set_profiling(True)
+    step(lp, zb, g)
+    stats = s.kernel_stats()
+    s.set_profiling(False)
+    hbm_peak, peak_kind = _peaks()
+    sweep_bytes, _ = s.traffic_model()
+    sw_cnt, sw_ms = stats["sweep"]
+    achieved = sweep_bytes / (sw_ms / sw_cnt * 1e-3) / 1e9
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    # FP64 form: time and agreement of the gradients and of z
+    g32 = g.double().cpu().numpy()
+    glam32, gom32 = res[1], res[2]
+    s64 = mk("fp64")
+    lp64 = lp.double()
+    zb64 = zb.double()
+    g64t = torch.empty_like(lp64)
+    s64.set_log_probs(lp64)
+    s64.backward(cfg.iters, zb64, every, out=g64t)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s64.set_log_probs(lp64)
+    _, glam64, gom64 = s64.backward(cfg.iters, zb64, every, out=g64t)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    g64 = g64t.cpu().numpy()
+    scale = max(np.abs(g64).max(), abs(glam64), np.abs(gom64).max())
+    grad_err = max(np.abs(g32 - g64).max(), abs(glam32 - glam64), np.abs(gom32 - gom64).max()) / scale
+    z32 = s.get_z()
+    z64 = s64.get_z()
+    s64.close()
+    # end to end with host buffers
+    lph = torch.tensor(np.log(sc.p), dtype=torch.float32).pin_memory()
+    zbh = zb.cpu().pin_memory()
+    gh = torch.empty_like(lph).pin_memory()
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(lph, zbh, gh)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_value = whole_job_rate(cfg.iters * len(e2e), world, max_over_ranks(sum(e2e), dev))
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, wall, cores = oracle_grad_sample()
+        cpu = {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
+               "sample": f"reference gradient (FP64 autograd through the oracle iteration) of a "
+                         f"64x64 crop, 50 iterations ({wall:.1f} s), scaled by pixel count"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": DIFF_DESC, "H": H, "W": W, "K": K, "iters": cfg.iters,
+                   "checkpoint_every": every, "unit_note": "differentiated iterations "
+                   "(forward + reverse pass) per second",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "forward_only_ms": float(np.mean(t_fwd)),
+        "gradient_vs_fp64": {"max_abs_error_over_max_entry": grad_err,
+                             "max_abs_z_vs_fp64": float(np.abs(z32 - z64).max())},
+        "fp64_form_ms_per_step": t64 * 1e3,
+        "roofline": {"bound": "hbm", "kernel": "sweep (fused prox + dual + rhs partials)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": sweep_bytes,
+                     "avg_launch_us": sw_ms / sw_cnt * 1e3},
+        "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
+        "kernel_timing": "CUDA events around every launch, eager replay of one step",
+        "dominant_kernel": dom[0],
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "ADMM iter/s", "h2d_bytes_per_step": 2 * 4 * H * W * K,
+                "d2h_bytes_per_step": 4 * H * W * K + 8 * 10},
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def run_reference_diff(args):
+    rates, cores, walls = [], 1, 0.0
+    for _ in range(args.warmup):
+        oracle_grad_sample()
+    for _ in range(args.steps):
+        r, wall, cores = oracle_grad_sample()
+        rates.append(r)
+        walls += wall
+    v = float(np.mean(rates))
+    sample = ("reference gradient of a 64x64 crop, 50 iterations, per step, scaled to 256x256 "
+              "by pixel count")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ADMM iter/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * walls / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": DIFF_DESC, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -845,7 +1044,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="145x145",
                     help="145x145 (default), 64x64, 2048x2048, HxW (K=16 synthetic scene), patchsweep, or "
-                         "batch64 (64 uneven images in one batch), or mlr610x340 (MLR front end)")
+                         "batch64 (64 uneven images in one batch), mlr610x340 (MLR front end), or diff256 "
+                         "(differentiable solver)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tilings")
     ap.add_argument("--tune-iters", type=int, default=4, help="batch64: iterations per trial")
     ap.add_argument("--cpu-iters", type=int, default=8)
@@ -871,6 +1071,8 @@ def main():
             run_batch(args, rank, world, local_rank)
         elif args.workload == "mlr610x340":
             run_mlr(args, rank, world, local_rank)
+        elif args.workload == "diff256":
+            run_diff(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -233,8 +233,8 @@ int segsalsa_str_linear_solve_static(const float* rhs, float* z, int32_t H, int3
  * device time in milliseconds since the last reset. Kernel kinds (index):
  *   0 fused sweep (prox + dual + rhs partials), 1 row FFT forward (with partial gather),
  *   2 column solve, 3 row FFT inverse, 4 diagnostics (residual / objective), 5 other,
- *   6 MLR class model (set_spectra).
- * launches and ms point to arrays of at least 7 entries (host memory). kernel_stats works
+ *   6 MLR class model (set_spectra), 7 reverse-pass kernels (backward).
+ * launches and ms point to arrays of at least 8 entries (host memory). kernel_stats works
  * with profiling off too; then ms is not filled. reset_stats zeroes both. */
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on);
 int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms);

@@ -29,7 +29,7 @@ SEGSALSA_G4_AFFINE = 0
 SEGSALSA_G4_SIMPLEX = 1
 
 KERNEL_KINDS = ("sweep", "row_fft_forward", "column_solve", "row_fft_inverse", "diagnostics",
-                "other", "mlr")
+                "other", "mlr", "adjoint")
 
 SYMBOLS = (
     "segsalsa_str_workspace_bytes", "segsalsa_str_create", "segsalsa_str_set_probs",

@@ -110,13 +110,12 @@ constexpr int ADJ_THREADS = 256;
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 template <typename T, int M, int G>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_vjp(const AdjArgs<T> a) {
+__global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) {
   constexpr int L = (2 * M + 1) * (2 * M + 1);
   constexpr int E = 2 * M + 2;
   constexpr int NP = L + 2;
-  __shared__ double red[NP];
-  for (int j = threadIdx.x; j < NP; j += blockDim.x) red[j] = 0.0;
-  __syncthreads();
+  constexpr int NWARP = ADJ_THREADS / 32;
+  __shared__ double red[NWARP][NP];
   const int H = a.s.H, W = a.s.W, K = a.s.K;
   const int g = threadIdx.x & (G - 1);
   const int pix = blockIdx.x * (ADJ_THREADS / G) + threadIdx.x / G;
@@ -242,14 +241,33 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_vjp(const AdjArgs<T> a) {
     const T z1 = a.zk1[e];
     s_loc = (double)((a.bbar[qh] - bc) * (a.zk1[qh] - z1) + (a.bbar[qv] - bc) * (a.zk1[qv] - z1));
   }
-  // block partial sums (tau once per pixel, from lane 0)
-  if (pok && g == 0) atomicAdd(&red[0], (double)gbar4[3]);
+  // block partial sums (tau once per pixel, from lane 0): warp shuffles, then the warps in a
+  // fixed order (deterministic)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto wsum = [&](double v) {
 #pragma unroll
-  for (int j = 0; j < L; ++j)
-    if (om_loc[j] != 0.0) atomicAdd(&red[1 + j], om_loc[j]);
-  if (s_loc != 0.0) atomicAdd(&red[L + 1], s_loc);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  {
+    const double t0 = wsum((pok && g == 0) ? (double)gbar4[3] : 0.0);
+    if (lane == 0) red[warp][0] = t0;
+  }
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const double t1 = wsum(om_loc[j]);
+    if (lane == 0) red[warp][1 + j] = t1;
+  }
+  {
+    const double t2 = wsum(s_loc);
+    if (lane == 0) red[warp][L + 1] = t2;
+  }
   __syncthreads();
-  for (int j = threadIdx.x; j < NP; j += blockDim.x) a.part[(size_t)blockIdx.x * NP + j] = red[j];
+  for (int j = threadIdx.x; j < NP; j += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < NWARP; ++w) t += red[w][j];
+    a.part[(size_t)blockIdx.x * NP + j] = t;
+  }
 }
 
 // zbar^k = G^T vbar^k = vbar1 + J^T vbar2 + vbar3 + vbar4, one thread per (pixel, class).

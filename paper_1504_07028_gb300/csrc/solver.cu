@@ -30,8 +30,8 @@
 namespace sgs {
 
 enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIAG = 4, KIND_OTHER = 5,
-            KIND_MLR = 6 };
-constexpr int NKIND = 7;
+            KIND_MLR = 6, KIND_ADJ = 7 };
+constexpr int NKIND = 8;
 constexpr int MAXCOV = 2;           // tile covers per row / column in the partial gather
 constexpr int TRACE_CAP = 128;      // device trace records before a flush to the host
 
@@ -1172,9 +1172,9 @@ class Solver : public SolverBase {
         a.mu = (T)mu;
         a.invK = (T)(1.0 / K);
         a.sp = sp;
-        SGS_LAUNCH(KIND_OTHER, launch_adj_vjp<T>(a, pl.M, pl.G, blocks, st));
+        SGS_LAUNCH(KIND_ADJ, launch_adj_vjp<T>(a, pl.M, pl.G, blocks, st));
         SGS_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * npart, cudaMemcpyDeviceToHost, st));
-        SGS_LAUNCH(KIND_OTHER, launch_adj_gt<T>(sh, pl.M, vcur, vcur + nloc, b.omega, zb, st));
+        SGS_LAUNCH(KIND_ADJ, launch_adj_gt<T>(sh, pl.M, vcur, vcur + nloc, b.omega, zb, st));
         SGS_CUDA(cudaStreamSynchronize(st));
         for (int bl = 0; bl < blocks; ++bl) {                   // fixed order: deterministic sums
           const double* q = hp.data() + (size_t)bl * (L + 2);
@@ -1187,7 +1187,7 @@ class Solver : public SolverBase {
       }
     }
     // z^1 = z^0 = p / 1^T p: the rest of zbar flows into log p
-    SGS_LAUNCH(KIND_OTHER, launch_adj_init<T>(sh, pl.G, b.p, zb, glp, st));
+    SGS_LAUNCH(KIND_ADJ, launch_adj_init<T>(sh, pl.G, b.p, zb, glp, st));
     if (layout == SEGSALSA_LAYOUT_HWK) {
       if ((rc = copy_out(glogp, glp, nK, dev))) return rc;
     } else {
