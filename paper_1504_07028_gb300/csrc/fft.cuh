@@ -701,9 +701,12 @@ inline bool make_fft_plan(int N, FftPlan<T>& pl) {
 template <typename T>
 inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_threads = 1024) {
   RowLaunch r{};
-  // one radix-8 butterfly (eight values) per thread and stage; fewer threads loop
+  // one radix-8 butterfly (eight values) per thread and stage; fewer threads loop. A direct
+  // prime stage (prime factor 11 .. 127) sums R terms per output in sequence: there, one
+  // thread per output keeps the chain short.
   const int elems = Mf * QB;
-  int t = (elems / 8 + 31) / 32 * 32;
+  const bool direct = !blue && largest_prime_factor(Mf) > 7;
+  int t = ((direct ? elems : elems / 8) + 31) / 32 * 32;
   const int cap = std::min(target_threads, 1024);
   r.threads = t < 64 ? 64 : (t > cap ? cap : t);
   r.tables = row_smem_bytes<T>(N, Mf, blue, QB, 1) <= 160 * 1024;

@@ -11,7 +11,7 @@ template <typename T> size_t MlrGrant<T>::g = 0;
 
 template <typename T>
 cudaError_t launch_mlr(const MlrArgs& a, cudaStream_t st) {
-  const size_t smem = mlr_smem_bytes(a.dpad, a.npad);
+  const size_t smem = mlr_smem_bytes(a.d, a.dpad, a.npad, a.K);
   if (smem > MlrGrant<T>::g) {
     const cudaError_t e =
         cudaFuncSetAttribute(k_mlr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

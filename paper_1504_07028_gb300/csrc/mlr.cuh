@@ -103,9 +103,46 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Dynamic shared memory of a CTA: A and B tiles, then the barrier and the TMEM slot.
-inline size_t mlr_smem_bytes(int dpad, int npad) {
+// Dynamic shared memory of a CTA: the A and B operand tiles, the barriers and the TMEM slot,
+// then the staging areas the tile's spectra (128 rows of d values) and the weights (K rows)
+// arrive in as laid out in memory.
+__host__ __device__ inline size_t mlr_stage_a_offset(int dpad, int npad) {
   return (size_t)(MLR_TILE + npad) * dpad * 2 + 64;
+}
+__host__ __device__ inline size_t mlr_stage_b_offset(int d, int dpad, int npad) {
+  return mlr_stage_a_offset(dpad, npad) + ((size_t)MLR_TILE * d * 2 + 15) / 16 * 16;
+}
+inline size_t mlr_smem_bytes(int d, int dpad, int npad, int K) {
+  return mlr_stage_b_offset(d, dpad, npad) + ((size_t)K * d * 2 + 15) / 16 * 16;
+}
+
+// Copy `bytes` from global src (16-byte aligned) to shared dst: the 16-byte multiple by one
+// bulk copy issued by thread 0 (counted into `tx`), the rest by plain loads of all threads.
+__device__ __forceinline__ void mlr_stage_run(unsigned char* dst, const unsigned char* src,
+                                              uint32_t bytes, uint64_t* bar) {
+  const uint32_t bulk = bytes & ~15u;
+  if (threadIdx.x == 0 && bulk) bulk_g2s(dst, src, bulk, bar);
+  for (uint32_t i = bulk + threadIdx.x; i < bytes; i += MLR_THREADS) dst[i] = __ldg(src + i);
+}
+
+// Thread r packs row r of a row-major staged matrix (rows of d BF16 values) into the
+// K-major core-matrix layout, 16 bytes (8 bands) per store; rows >= rows_valid and bands >= d
+// are zero.
+__device__ __forceinline__ void mlr_pack_row(unsigned char* dst, const unsigned char* staged,
+                                             int r, int rows_valid, int d, int kc) {
+  const uint16_t* srow = reinterpret_cast<const uint16_t*>(staged) + (size_t)r * d;
+  const bool rv = r < rows_valid;
+  for (int c = 0; c < kc; ++c) {
+    uint32_t w4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k0 = 8 * c + 2 * e;
+      const uint32_t lo = (rv && k0 < d) ? srow[k0] : 0u;
+      const uint32_t hi = (rv && k0 + 1 < d) ? srow[k0 + 1] : 0u;
+      w4[e] = lo | (hi << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + mlr_canon_off(r, 8 * c, kc)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
 }
 
 template <typename T>
@@ -114,31 +151,34 @@ __global__ void __launch_bounds__(MLR_THREADS) k_mlr(const MlrArgs a) {
   unsigned char* As = smem_raw;
   unsigned char* Bs = As + (size_t)MLR_TILE * a.dpad * 2;
   uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)a.npad * a.dpad * 2);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* lbar = bar + 1;                      // completion of the staging copies
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  unsigned char* stA = smem_raw + mlr_stage_a_offset(a.dpad, a.npad);
+  unsigned char* stB = smem_raw + mlr_stage_b_offset(a.d, a.dpad, a.npad);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kc = a.dpad >> 3;
   const int row0 = blockIdx.x * MLR_TILE;
+  const int rows = min(MLR_TILE, a.n - row0);
+  // the tile's spectra are one contiguous run of rows * d values starting at byte
+  // row0 * d * 2 (a multiple of 256) of the 16-byte aligned x; the weights likewise
+  const uint32_t bytesA = (uint32_t)rows * a.d * 2, bytesB = (uint32_t)a.K * a.d * 2;
+  const unsigned char* srcA = reinterpret_cast<const unsigned char*>(a.x + (size_t)row0 * a.d);
+  const unsigned char* srcB = reinterpret_cast<const unsigned char*>(a.w);
 
   if (warp == 0) tmem_alloc(slot, MLR_TMEM_COLS);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
+    mbar_init(lbar, 1);
     mbar_fence_init();
+    mbar_arrive_expect_tx(lbar, (bytesA & ~15u) + (bytesB & ~15u));
   }
-  // stage A: warp w fills rows w, w+4, ...; lanes stride along the bands (coalesced reads)
-  for (int r = warp; r < MLR_TILE; r += MLR_THREADS / 32) {
-    const int row = row0 + r;
-    const uint16_t* src = a.x + (size_t)row * a.d;
-    for (int k = lane; k < a.dpad; k += 32) {
-      const uint16_t v = (row < a.n && k < a.d) ? __ldg(src + k) : (uint16_t)0;
-      *reinterpret_cast<uint16_t*>(As + mlr_canon_off(r, k, kc)) = v;
-    }
-  }
-  // stage B: the weights, zero rows for the padded classes
-  for (int e = threadIdx.x; e < a.npad * a.dpad; e += MLR_THREADS) {
-    const int r = e / a.dpad, k = e - r * a.dpad;
-    const uint16_t v = (r < a.K && k < a.d) ? __ldg(a.w + (size_t)r * a.d + k) : (uint16_t)0;
-    *reinterpret_cast<uint16_t*>(Bs + mlr_canon_off(r, k, kc)) = v;
-  }
+  mlr_stage_run(stA, srcA, bytesA, lbar);
+  mlr_stage_run(stB, srcB, bytesB, lbar);
+  __syncthreads();                                // barrier init and the tail bytes
+  const bool staged = mbar_wait_bounded(lbar, 0, WAIT_BUDGET_CYCLES);
+  if (!staged && threadIdx.x == 0) atomicExch(a.err, 1);
+  mlr_pack_row(As, stA, threadIdx.x, staged ? rows : 0, a.d, kc);
+  if (threadIdx.x < a.npad) mlr_pack_row(Bs, stB, threadIdx.x, staged ? a.K : 0, a.d, kc);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();

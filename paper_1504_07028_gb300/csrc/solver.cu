@@ -628,26 +628,30 @@ class Solver : public SolverBase {
     const uint16_t* xd = static_cast<const uint16_t*>(x);
     const uint16_t* wd = static_cast<const uint16_t*>(w);
     const float* bd = bias;
-    if (!dev) {
-      const size_t need = align_up(xb, 256) + align_up(wb, 256) + bb;
-      if (need > mlr_cap) {
-        if (mlr_buf) cudaFree(mlr_buf);
-        mlr_buf = nullptr;
-        mlr_cap = 0;
-        cudaError_t e = cudaMalloc(&mlr_buf, need);
-        if (e != cudaSuccess) { mlr_buf = nullptr; return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
-        mlr_cap = need;
-      }
-      char* base = static_cast<char*>(mlr_buf);
-      SGS_CUDA(cudaMemcpyAsync(base, x, xb, cudaMemcpyHostToDevice, st));
-      SGS_CUDA(cudaMemcpyAsync(base + align_up(xb, 256), w, wb, cudaMemcpyHostToDevice, st));
+    // the kernel bulk-copies x and w from 16-byte aligned addresses: the weights always go
+    // through the handle's staging buffer, x when it is host data or not so aligned
+    const bool stage_x = !dev || (reinterpret_cast<uintptr_t>(x) & 15) != 0;
+    const size_t need = align_up(xb, 256) + align_up(wb, 256) + bb;
+    if (need > mlr_cap) {
+      if (mlr_buf) cudaFree(mlr_buf);
+      mlr_buf = nullptr;
+      mlr_cap = 0;
+      cudaError_t e = cudaMalloc(&mlr_buf, need);
+      if (e != cudaSuccess) { mlr_buf = nullptr; return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+      mlr_cap = need;
+    }
+    char* base = static_cast<char*>(mlr_buf);
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (stage_x) {
+      SGS_CUDA(cudaMemcpyAsync(base, x, xb, kind, st));
       xd = reinterpret_cast<const uint16_t*>(base);
-      wd = reinterpret_cast<const uint16_t*>(base + align_up(xb, 256));
-      if (bias) {
-        float* bdev = reinterpret_cast<float*>(base + align_up(xb, 256) + align_up(wb, 256));
-        SGS_CUDA(cudaMemcpyAsync(bdev, bias, bb, cudaMemcpyHostToDevice, st));
-        bd = bdev;
-      }
+    }
+    SGS_CUDA(cudaMemcpyAsync(base + align_up(xb, 256), w, wb, kind, st));
+    wd = reinterpret_cast<const uint16_t*>(base + align_up(xb, 256));
+    if (bias && !dev) {
+      float* bdev = reinterpret_cast<float*>(base + align_up(xb, 256) + align_up(wb, 256));
+      SGS_CUDA(cudaMemcpyAsync(bdev, bias, bb, kind, st));
+      bd = bdev;
     }
     MlrArgs a{};
     a.x = xd; a.w = wd; a.bias = bd; a.p = b.tmp; a.err = b.err;

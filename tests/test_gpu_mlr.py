@@ -75,6 +75,17 @@ def test_mlr_host_and_device_inputs_agree(B):
     torch.cuda.synchronize()
     s.set_spectra(xd, wd)
     assert np.array_equal(s.get_probs(), p_host)
+    # device spectra and weights that do not start on a 16-byte boundary (views one value in)
+    big = torch.empty(xd.numel() + 1, dtype=torch.bfloat16, device="cuda")
+    big[1:] = xd.reshape(-1)
+    xm = big[1:].view(xd.shape)
+    bigw = torch.empty(wd.numel() + 1, dtype=torch.bfloat16, device="cuda")
+    bigw[1:] = wd.reshape(-1)
+    wm = bigw[1:].view(wd.shape)
+    assert xm.data_ptr() % 16 != 0 and wm.data_ptr() % 16 != 0
+    torch.cuda.synchronize()
+    s.set_spectra(xm, wm)
+    assert np.array_equal(s.get_probs(), p_host)
     s.close()
 
 
