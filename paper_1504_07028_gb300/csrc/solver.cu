@@ -733,7 +733,6 @@ class Solver : public SolverBase {
   int ensure_trace_host(int n) {
     if (n <= trace_host_cap) return SEGSALSA_OK;
     if (trace_host) cudaFreeHost(trace_host);
-    if (mlr_buf) cudaFree(mlr_buf);
     trace_host = nullptr;
     trace_host_cap = 0;
     SGS_CUDA(cudaMallocHost(&trace_host, sizeof(double) * 6 * (size_t)n));

@@ -130,3 +130,26 @@ def test_mlr_rejects_bad_input(B):
     assert e.value.code == B.SEGSALSA_ERR_ARG
     assert s.get_iteration() == 3 and np.array_equal(s.get_z(), z0)
     s.close()
+
+
+def test_mlr_staging_survives_traced_solves(B):
+    """The handle's staging buffer for the weights outlives traced solves that grow the pinned
+    trace buffer: front end, traced solve, front end again (same and new spectra) on one handle
+    gives the probabilities of a fresh handle every time."""
+    import torch
+    H, W, K, d = 21, 19, 6, 40
+    sc = synth.mlr_scene(H, W, K, d, S=4, seed=64)
+    sc2 = synth.mlr_scene(H, W, K, d, S=4, seed=65)
+    s = _solver(B, H, W, K)
+    for i, (scn, iters, every) in enumerate([(sc, 20, 10), (sc, 200, 5), (sc2, 30, 1), (sc, 5, 1)]):
+        x, w = _bf16(scn.x), _bf16(scn.Wc)
+        torch.cuda.synchronize()
+        s.set_spectra(x, w)
+        p = s.get_probs()
+        fresh = _solver(B, H, W, K)
+        fresh.set_spectra(x, w)
+        assert np.array_equal(p, fresh.get_probs()), i
+        fresh.close()
+        tr = s.solve(iters, trace_every=every)
+        assert len(tr) >= iters // every
+    s.close()
