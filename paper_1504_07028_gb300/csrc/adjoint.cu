@@ -65,6 +65,31 @@ cudaError_t launch_exp_logp(AdjShape s, int G, const T* logp, T* p, cudaStream_t
   return cudaGetLastError();
 }
 
+// One block per column of the partials; each thread adds a strided set of rows, then the warps'
+// shuffle sums in warp order: the same inputs always give the same bits.
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_sum(const double* part, int blocks,
+                                                          double* acc) {
+  __shared__ double red[ADJ_THREADS / 32];
+  const double* col = part + (size_t)blockIdx.x * blocks;
+  double t = 0.0;
+  for (int r = threadIdx.x; r < blocks; r += ADJ_THREADS) t += col[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < ADJ_THREADS / 32; ++w) s += red[w];
+    acc[blockIdx.x] += s;
+  }
+}
+
+cudaError_t launch_adj_sum(const double* part, int blocks, int np, double* acc, cudaStream_t st) {
+  if (np < 1 || blocks < 1) return cudaErrorInvalidValue;
+  k_adj_sum<<<np, ADJ_THREADS, 0, st>>>(part, blocks, acc);
+  return cudaGetLastError();
+}
+
 #define SGS_ADJ_INST(T)                                                                       \
   template cudaError_t launch_adj_vjp<T>(const AdjArgs<T>&, int, int, int, cudaStream_t);     \
   template cudaError_t launch_adj_gt<T>(AdjShape, int, const T*, const T*, const T*, T*,      \

@@ -99,13 +99,29 @@ struct AdjArgs {
   T* v_loc;           // out: vbar^k [n][3][K]
   T* v_2;             // out: vbar^k [n][L][K][2]
   T* glogp;           // accumulated d/dlog p [n][K]
-  double* part;       // per block: tau, omega_0..omega_{L-1}, S (= <D bbar, D z^{k+1}>)
+  double* part;       // block partials [NP][blocks]: tau, omega_0..omega_{L-1}, S (= <D bbar, D z^{k+1}>)
   const T* omega;
   T tau, mu, invK;
   int sp;
 };
 
 constexpr int ADJ_THREADS = 256;
+
+// The (h, v) pair of one class in the [..][K][2] layouts, moved as one 8- or 16-byte access.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using t = float2; };
+template <> struct Pair2<double> { using t = double2; };
+template <typename T>
+__device__ __forceinline__ typename Pair2<T>::t ld_pair(const T* q) {
+  return __ldg(reinterpret_cast<const typename Pair2<T>::t*>(q));
+}
+template <typename T>
+__device__ __forceinline__ void st_pair(T* q, T h, T v) {
+  typename Pair2<T>::t o;
+  o.x = h;
+  o.y = v;
+  *reinterpret_cast<typename Pair2<T>::t*>(q) = o;
+}
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -146,8 +162,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) 
   for (int j = 0; j < L; ++j) {
     const int dy = j / (2 * M + 1), dx = j % (2 * M + 1);
     const T w = a.omega[j];
-    const T dh = kok ? a.d2[e2 + (size_t)j * K * 2] : T(0);
-    const T dv = kok ? a.d2[e2 + (size_t)j * K * 2 + 1] : T(0);
+    T dh = T(0), dv = T(0);
+    if (kok) {
+      const auto q = ld_pair(a.d2 + e2 + (size_t)j * K * 2);
+      dh = q.x;
+      dv = q.y;
+    }
     vh[j] = w * (zw[dy][dx + 1] - zw[dy][dx]) - dh;
     vv[j] = w * (zw[dy + 1][dx] - zw[dy][dx]) - dv;
   }
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) 
   const T vb4 = -bc + nd4 + (ub4 - sub4 * a.invK);
   (void)s4;
   // block 2 (Schatten prox): ubar2 = 2 J bbar - vbar2^{k+1}
-  T ubh[L], ubv[L], jbh[L], jbv[L];
+  T jbh[L], jbv[L];
   T Ab11 = T(0), Ab12 = T(0), Ab22 = T(0);
 #pragma unroll
   for (int j = 0; j < L; ++j) {
@@ -196,40 +216,47 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) 
     const T w = a.omega[j];
     jbh[j] = bw[dy][dx + 1] - bw[dy][dx];             // unweighted S_j D bbar
     jbv[j] = bw[dy + 1][dx] - bw[dy][dx];
-    const T nh = a.vn_2 && kok ? a.vn_2[e2 + (size_t)j * K * 2] : T(0);
-    const T nv = a.vn_2 && kok ? a.vn_2[e2 + (size_t)j * K * 2 + 1] : T(0);
-    ubh[j] = T(2) * w * jbh[j] - nh;
-    ubv[j] = T(2) * w * jbv[j] - nv;
-    Ab11 += ubh[j] * vh[j];
-    Ab12 += ubh[j] * vv[j] + ubv[j] * vh[j];
-    Ab22 += ubv[j] * vv[j];
+    T nh = T(0), nv = T(0);
+    if (a.vn_2 && kok) {
+      const auto q = ld_pair(a.vn_2 + e2 + (size_t)j * K * 2);
+      nh = q.x;
+      nv = q.y;
+    }
+    const T ubh = T(2) * w * jbh[j] - nh, ubv = T(2) * w * jbv[j] - nv;
+    Ab11 += ubh * vh[j];
+    Ab12 += ubh * vv[j] + ubv * vh[j];
+    Ab22 += ubv * vv[j];
   }
   Ab11 = group_sum<G>(Ab11); Ab12 = group_sum<G>(Ab12); Ab22 = group_sum<G>(Ab22);
   T gbar4[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) gbar4[m] = Ab11 * A11.d[m] + Ab12 * A12.d[m] + Ab22 * A22.d[m];
-  double om_loc[L];
-  double s_loc = 0.0;
+  // per-thread terms of the parameter gradients, in the working precision (FP64 only from the
+  // warp sums on: FP64 arithmetic is scarce on this part)
+  T om_loc[L];
+  T s_loc = T(0);
 #pragma unroll
   for (int j = 0; j < L; ++j) {
     const int dy = j / (2 * M + 1), dx = j % (2 * M + 1);
     const T w = a.omega[j];
-    const T nh = a.vn_2 && kok ? a.vn_2[e2 + (size_t)j * K * 2] : T(0);
-    const T nv = a.vn_2 && kok ? a.vn_2[e2 + (size_t)j * K * 2 + 1] : T(0);
-    const T Vh = ubh[j] * A11.v + ubv[j] * A12.v + T(2) * gbar4[0] * vh[j] + gbar4[1] * vv[j];
-    const T Vv = ubh[j] * A12.v + ubv[j] * A22.v + gbar4[1] * vh[j] + T(2) * gbar4[2] * vv[j];
+    T nh = T(0), nv = T(0);
+    if (a.vn_2 && kok) {
+      const auto q = ld_pair(a.vn_2 + e2 + (size_t)j * K * 2);
+      nh = q.x;
+      nv = q.y;
+    }
+    const T ubh = T(2) * w * jbh[j] - nh, ubv = T(2) * w * jbv[j] - nv;   // as in the loop above
+    const T Vh = ubh * A11.v + ubv * A12.v + T(2) * gbar4[0] * vh[j] + gbar4[1] * vv[j];
+    const T Vv = ubh * A12.v + ubv * A22.v + gbar4[1] * vh[j] + T(2) * gbar4[2] * vv[j];
     const T vbh = -w * jbh[j] + nh + Vh;
     const T vbv = -w * jbv[j] + nv + Vv;
-    if (kok) {
-      a.v_2[e2 + (size_t)j * K * 2] = vbh;
-      a.v_2[e2 + (size_t)j * K * 2 + 1] = vbv;
-    }
+    if (kok) st_pair(a.v_2 + e2 + (size_t)j * K * 2, vbh, vbv);
     // omega_j: v2 = omega_j S_j D z^k - d2 (first term); b = G^T w with w2 = 2 u2 - v2 (second)
     const T zdh = zw[dy][dx + 1] - zw[dy][dx], zdv = zw[dy + 1][dx] - zw[dy][dx];
     const T u2h = vh[j] * A11.v + vv[j] * A12.v, u2v = vh[j] * A12.v + vv[j] * A22.v;
-    om_loc[j] = kok ? (double)(vbh * zdh + vbv * zdv) +
-                          (double)(jbh[j] * (T(2) * u2h - vh[j]) + jbv[j] * (T(2) * u2v - vv[j]))
-                    : 0.0;
+    om_loc[j] = kok ? (vbh * zdh + vbv * zdv) +
+                          (jbh[j] * (T(2) * u2h - vh[j]) + jbv[j] * (T(2) * u2v - vv[j]))
+                    : T(0);
   }
   if (kok) {
     a.v_loc[el] = vb1;
@@ -239,34 +266,34 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) 
     const size_t qh = ((size_t)y * W + wrapi(x + 1, W)) * K + g;
     const size_t qv = ((size_t)wrapi(y + 1, H) * W + x) * K + g;
     const T z1 = a.zk1[e];
-    s_loc = (double)((a.bbar[qh] - bc) * (a.zk1[qh] - z1) + (a.bbar[qv] - bc) * (a.zk1[qv] - z1));
+    s_loc = (a.bbar[qh] - bc) * (a.zk1[qh] - z1) + (a.bbar[qv] - bc) * (a.zk1[qv] - z1);
   }
-  // block partial sums (tau once per pixel, from lane 0): warp shuffles, then the warps in a
-  // fixed order (deterministic)
+  // block partial sums (tau once per pixel, from lane 0): warp shuffles in the working
+  // precision, then the warps in a fixed order in FP64 (deterministic)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  auto wsum = [&](double v) {
+  auto wsum = [&](T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
   };
   {
-    const double t0 = wsum((pok && g == 0) ? (double)gbar4[3] : 0.0);
-    if (lane == 0) red[warp][0] = t0;
+    const T t0 = wsum((pok && g == 0) ? gbar4[3] : T(0));
+    if (lane == 0) red[warp][0] = (double)t0;
   }
 #pragma unroll
   for (int j = 0; j < L; ++j) {
-    const double t1 = wsum(om_loc[j]);
-    if (lane == 0) red[warp][1 + j] = t1;
+    const T t1 = wsum(om_loc[j]);
+    if (lane == 0) red[warp][1 + j] = (double)t1;
   }
   {
-    const double t2 = wsum(s_loc);
-    if (lane == 0) red[warp][L + 1] = t2;
+    const T t2 = wsum(s_loc);
+    if (lane == 0) red[warp][L + 1] = (double)t2;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < NP; j += blockDim.x) {
     double t = 0.0;
     for (int w = 0; w < NWARP; ++w) t += red[w][j];
-    a.part[(size_t)blockIdx.x * NP + j] = t;
+    a.part[(size_t)j * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -337,5 +364,8 @@ cudaError_t launch_adj_init(AdjShape s, int G, const T* p, const T* zbar, T* glo
                             cudaStream_t st);
 template <typename T>
 cudaError_t launch_exp_logp(AdjShape s, int G, const T* logp, T* p, cudaStream_t st);
+// acc[j] += sum over the `blocks` partials of column j of part ([np][blocks]), one block per
+// column, in a fixed order.
+cudaError_t launch_adj_sum(const double* part, int blocks, int np, double* acc, cudaStream_t st);
 
 }  // namespace sgs

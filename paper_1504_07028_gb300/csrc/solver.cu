@@ -1068,28 +1068,30 @@ class Solver : public SolverBase {
     const size_t npart = (size_t)blocks * (L + 2);
     // device memory of the pass (released at the end)
     Carver cv{nullptr};
-    auto plan = [&](Carver& c, T*& ck, T*& fin, T*& zs, T*& dls, T*& d2s, T*& vb, T*& zb, T*& bb,
-                    T*& glp, double*& part) {
+    auto plan = [&](Carver& c, T*& ck, T*& fin, T*& zs, T*& dls, T*& d2s, T*& vbl, T*& vb2,
+                    T*& zb, T*& bb, T*& glp, double*& part, double*& acc) {
       ck = c.take<T>((size_t)nseg * st_elems);
       fin = c.take<T>(st_elems);
       zs = c.take<T>((size_t)(every + 2) * nK);
       dls = c.take<T>((size_t)(every + 1) * nloc);
       d2s = c.take<T>((size_t)(every + 1) * n2);
-      vb = c.take<T>(2 * (nloc + n2));
+      vbl = c.take<T>(2 * nloc);   // vbar local blocks, two buffers
+      vb2 = c.take<T>(2 * n2);     // vbar d2 blocks, two buffers (pairs stay 2 T aligned)
       zb = c.take<T>(nK);
       bb = c.take<T>(nK);
       glp = c.take<T>(nK);
       part = c.take<double>(npart);
+      acc = c.take<double>(L + 2);
     };
-    T *ck, *fin, *zs, *dls, *d2s, *vb, *zb, *bb, *glp;
-    double* part;
-    plan(cv, ck, fin, zs, dls, d2s, vb, zb, bb, glp, part);
+    T *ck, *fin, *zs, *dls, *d2s, *vbl, *vb2, *zb, *bb, *glp;
+    double *part, *acc;
+    plan(cv, ck, fin, zs, dls, d2s, vbl, vb2, zb, bb, glp, part, acc);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, cv.off);
     if (e != cudaSuccess) return fail(SEGSALSA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     struct Free { void* m; ~Free() { cudaFree(m); } } guard{mem};
     Carver cm{static_cast<char*>(mem)};
-    plan(cm, ck, fin, zs, dls, d2s, vb, zb, bb, glp, part);
+    plan(cm, ck, fin, zs, dls, d2s, vbl, vb2, zb, bb, glp, part, acc);
     auto save = [&](T* dst) -> cudaError_t {
       cudaError_t r;
       if ((r = cudaMemcpyAsync(dst, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st))) return r;
@@ -1124,9 +1126,7 @@ class Solver : public SolverBase {
       SGS_LAUNCH(KIND_OTHER, (k_khw_to_hwk<T><<<grid1(nK), AUX_THREADS, 0, st>>>(b.tmp, zb, n, K)));
     }
     SGS_CUDA(cudaMemsetAsync(glp, 0, sizeof(T) * nK, st));
-    std::vector<double> hp(npart);
-    double tau_bar = 0.0, s_bar = 0.0;
-    std::vector<double> om_bar(L, 0.0);
+    SGS_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (L + 2), st));
     const AdjShape sh{pl.H, pl.W, K, n};
     bool first = true;
     int cur = 0;
@@ -1162,12 +1162,14 @@ class Solver : public SolverBase {
         a.dloc = dls + (size_t)(i - 1) * nloc;
         a.d2 = d2s + (size_t)(i - 1) * n2;
         a.bbar = bb;
-        T* vcur = vb + (size_t)cur * (nloc + n2);
-        T* vprev = vb + (size_t)(cur ^ 1) * (nloc + n2);
-        a.vn_loc = first ? nullptr : vprev;
-        a.vn_2 = first ? nullptr : vprev + nloc;
-        a.v_loc = vcur;
-        a.v_2 = vcur + nloc;
+        a.vn_loc = first ? nullptr : vbl + (size_t)(cur ^ 1) * nloc;
+        a.vn_2 = first ? nullptr : vb2 + (size_t)(cur ^ 1) * n2;
+        a.v_loc = vbl + (size_t)cur * nloc;
+        a.v_2 = vb2 + (size_t)cur * n2;
+        // the (h, v) pairs of the d2 layouts move as single 2 T accesses
+        const uintptr_t pairs = reinterpret_cast<uintptr_t>(a.d2) | reinterpret_cast<uintptr_t>(a.v_2) |
+                                reinterpret_cast<uintptr_t>(a.vn_2);
+        if (pairs & (2 * sizeof(T) - 1)) return fail(SEGSALSA_ERR_CUDA, "reverse pass: unaligned d2 buffers");
         a.glogp = glp;
         a.part = part;
         a.omega = b.omega;
@@ -1176,15 +1178,10 @@ class Solver : public SolverBase {
         a.invK = (T)(1.0 / K);
         a.sp = sp;
         SGS_LAUNCH(KIND_ADJ, launch_adj_vjp<T>(a, pl.M, pl.G, blocks, st));
-        SGS_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * npart, cudaMemcpyDeviceToHost, st));
-        SGS_LAUNCH(KIND_ADJ, launch_adj_gt<T>(sh, pl.M, vcur, vcur + nloc, b.omega, zb, st));
-        SGS_CUDA(cudaStreamSynchronize(st));
-        for (int bl = 0; bl < blocks; ++bl) {                   // fixed order: deterministic sums
-          const double* q = hp.data() + (size_t)bl * (L + 2);
-          tau_bar += q[0];
-          for (int j = 0; j < L; ++j) om_bar[j] += q[1 + j];
-          s_bar += q[L + 1];
-        }
+        // the unit's block partials into the running FP64 sums; units run in the order
+        // k = iters - 1 .. 1 whatever the checkpoint interval, so the sums are too
+        SGS_LAUNCH(KIND_ADJ, launch_adj_sum(part, blocks, L + 2, acc, st));
+        SGS_LAUNCH(KIND_ADJ, launch_adj_gt<T>(sh, pl.M, a.v_loc, a.v_2, b.omega, zb, st));
         first = false;
         cur ^= 1;
       }
@@ -1201,10 +1198,12 @@ class Solver : public SolverBase {
     SGS_CUDA(load(fin));
     iter = iters;
     rhs_dense = false;
+    std::vector<double> sums(L + 2);   // tau, omega_0..omega_{L-1}, S
+    SGS_CUDA(cudaMemcpyAsync(sums.data(), acc, sizeof(double) * (L + 2), cudaMemcpyDeviceToHost, st));
     SGS_CUDA(cudaStreamSynchronize(st));
-    if (glam) *glam = tau_bar / mu;
+    if (glam) *glam = sums[0] / mu;
     if (gom)
-      for (int j = 0; j < L; ++j) gom[j] = om_bar[j] - 2.0 * omega[j] * s_bar;
+      for (int j = 0; j < L; ++j) gom[j] = sums[1 + j] - 2.0 * omega[j] * sums[L + 1];
     return SEGSALSA_OK;
   }
 
