@@ -224,7 +224,8 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   }
   if (pl.Mf > 8192) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
   const int Q = (K + 1) / 2;
-  // small images (latency bound): fewer class pairs per CTA so the grid covers the GPU;
+  // small images (latency bound): fewer class pairs per CTA until the grid has one CTA per SM
+  // (a target of eight per SM, i.e. one pair per CTA, measured 12 % slower at 145 x 145, K = 16);
   // larger ones: as many as fit (contiguous 64-byte pixel reads, fewer CTAs)
   const bool small_image = (long long)H * W < 65536;
   pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
@@ -245,8 +246,8 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.CB = sizeof(T) == 4 ? 8 : 4;
   while ((size_t)H * pl.CB * sizeof(cplx<T>) > 64 * 1024 && pl.CB > 1) pl.CB /= 2;
   if ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024) { msg = "image too tall for the column solve"; return SEGSALSA_ERR_ARG; }
-  // small images: thinner column blocks so that the grid covers the GPU
-  while (small_image && pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 8 * 152) pl.CB /= 2;
+  // small images: thinner column blocks until the grid has one CTA per SM
+  while (small_image && pl.CB > 1 && (long long)pl.Wh * K / pl.CB < 152) pl.CB /= 2;
   if (tl && tl->col_block) {
     pl.CB = floor_pow2(tl->col_block);
     while ((size_t)H * pl.CB * sizeof(cplx<T>) > 200 * 1024 && pl.CB > 1) pl.CB /= 2;
