@@ -233,8 +233,9 @@ int segsalsa_str_linear_solve_static(const float* rhs, float* z, int32_t H, int3
  * device time in milliseconds since the last reset. Kernel kinds (index):
  *   0 fused sweep (prox + dual + rhs partials), 1 row FFT forward (with partial gather),
  *   2 column solve, 3 row FFT inverse, 4 diagnostics (residual / objective), 5 other,
- *   6 MLR class model (set_spectra), 7 reverse-pass kernels (backward).
- * launches and ms point to arrays of at least 8 entries (host memory). kernel_stats works
+ *   6 MLR class model (set_spectra), 7 reverse-pass kernels (backward), 8 z-update fused
+ *   over a thread-block cluster (replaces 1-3 where the tiling selects it).
+ * launches and ms point to arrays of at least 9 entries (host memory). kernel_stats works
  * with profiling off too; then ms is not filled. reset_stats zeroes both. */
 int segsalsa_str_set_profiling(segsalsa_str_t* h, int32_t on);
 int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms);
@@ -261,13 +262,20 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
  *   col_block   : frequency columns per column-solve CTA, a power of two 1..8
  *   row_threads : target threads of a row-transform CTA, 64..1024 (rounded down to a power
  *                 of two; a CTA gets more when a thread would hold over 16 values)
- *   col_rows    : rows per segment of the column recursions, 2..4096 */
+ *   col_rows    : rows per segment of the column recursions, 2..4096
+ *   zfuse       : z-update (12) in one launch over a thread-block cluster of this many CTAs,
+ *                 each owning a band of rows whose transforms and spectra stay in shared
+ *                 memory (2, 4, 8 or 16); 1 = three launches (row transforms, column solves,
+ *                 inverse row transforms); 0 = the library's choice (three launches: the
+ *                 fused form measured slower on every shape tried). A fused request that the
+ *                 band or the device cannot hold runs three launches (get_tiling reports 1). */
 typedef struct {
   int32_t tile_rows;
   int32_t row_pairs;
   int32_t col_block;
   int32_t row_threads;
   int32_t col_rows;
+  int32_t zfuse;
 } segsalsa_str_tiling;
 
 /* create / workspace_bytes with an explicit tiling (NULL = defaults, same as the plain calls).

@@ -29,7 +29,7 @@ SEGSALSA_G4_AFFINE = 0
 SEGSALSA_G4_SIMPLEX = 1
 
 KERNEL_KINDS = ("sweep", "row_fft_forward", "column_solve", "row_fft_inverse", "diagnostics",
-                "other", "mlr", "adjoint")
+                "other", "mlr", "adjoint", "zupdate_fused")
 
 SYMBOLS = (
     "segsalsa_str_workspace_bytes", "segsalsa_str_create", "segsalsa_str_set_probs",
@@ -59,16 +59,18 @@ class Params(C.Structure):
 
 class Tiling(C.Structure):
     _fields_ = [("tile_rows", C.c_int32), ("row_pairs", C.c_int32), ("col_block", C.c_int32),
-                ("row_threads", C.c_int32), ("col_rows", C.c_int32)]
+                ("row_threads", C.c_int32), ("col_rows", C.c_int32), ("zfuse", C.c_int32)]
 
     def as_tuple(self):
-        return (self.tile_rows, self.row_pairs, self.col_block, self.row_threads, self.col_rows)
+        return (self.tile_rows, self.row_pairs, self.col_block, self.row_threads, self.col_rows,
+                self.zfuse)
 
 
-def make_tiling(tile_rows=0, row_pairs=0, col_block=0, row_threads=0, col_rows=0) -> Tiling:
+def make_tiling(tile_rows=0, row_pairs=0, col_block=0, row_threads=0, col_rows=0,
+                zfuse=0) -> Tiling:
     t = Tiling()
     t.tile_rows, t.row_pairs, t.col_block = int(tile_rows), int(row_pairs), int(col_block)
-    t.row_threads, t.col_rows = int(row_threads), int(col_rows)
+    t.row_threads, t.col_rows, t.zfuse = int(row_threads), int(col_rows), int(zfuse)
     return t
 
 

@@ -1,10 +1,12 @@
 // FP32 instantiations of the row-transform and column-solve passes.
 #define SGS_FFT_INSTANTIATE
-#include "fft.cuh"
+#include "zfused.cuh"
 
 namespace sgs {
 template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
 template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
+template cudaError_t launch_zfused<float>(const ZfArgs<float>&, int, int, size_t, cudaStream_t);
+template int zfused_max_clusters<float>(int, int, size_t);
 
 }  // namespace sgs

@@ -23,6 +23,7 @@
 #include "../../include/segsalsa_str.h"
 #include "aux.cuh"
 #include "fft.cuh"
+#include "zfused.cuh"
 #include "launch.h"
 #include "mlr.cuh"
 #include "adjoint.cuh"
@@ -30,8 +31,8 @@
 namespace sgs {
 
 enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIAG = 4, KIND_OTHER = 5,
-            KIND_MLR = 6, KIND_ADJ = 7 };
-constexpr int NKIND = 8;
+            KIND_MLR = 6, KIND_ADJ = 7, KIND_ZF = 8 };
+constexpr int NKIND = 9;
 constexpr int MAXCOV = 2;           // tile covers per row / column in the partial gather
 constexpr int TRACE_CAP = 128;      // device trace records before a flush to the host
 
@@ -133,6 +134,9 @@ struct Plan {
   int CB, NSEG, col_threads, ncolblk;
   int row_threads, col_rows;   // target threads of a row-pass CTA; rows per column segment
   size_t col_smem;
+  // z-update fused over a cluster (0: three passes), its class-pair groups, threads, memory
+  int zf_cs, zf_qg, zf_rmax, zf_groups, zf_threads;
+  size_t zf_smem;
   int nproj_blk, nprior_blk, ngsq_blk;
   std::vector<int> covY, covX;  // [H][MAXCOV], [W][MAXCOV]
 };
@@ -160,6 +164,9 @@ static int check_tiling(const segsalsa_str_tiling* t, std::string& msg) {
   if (t->col_block < 0 || t->col_block > 8) { msg = "col_block must be 0..8"; return SEGSALSA_ERR_ARG; }
   if (t->row_threads && (t->row_threads < 64 || t->row_threads > 1024)) { msg = "row_threads must be 0 or 64..1024"; return SEGSALSA_ERR_ARG; }
   if (t->col_rows && (t->col_rows < 2 || t->col_rows > 4096)) { msg = "col_rows must be 0 or 2..4096"; return SEGSALSA_ERR_ARG; }
+  if (t->zfuse && t->zfuse != 1 && t->zfuse != 2 && t->zfuse != 4 && t->zfuse != 8 && t->zfuse != 16) {
+    msg = "zfuse must be 0, 1, 2, 4, 8 or 16"; return SEGSALSA_ERR_ARG;
+  }
   return SEGSALSA_OK;
 }
 
@@ -261,6 +268,33 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.NSEG = std::max(1, std::min(H / pl.col_rows, 1024 / nseq));
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
+  // z-update in one launch, on request only (measured slower than the three passes at every
+  // shape tried): clusters of CS CTAs (one band of rows each) per class pair, when a band's
+  // transforms and half spectra fit in shared memory (the handle falls back to three passes
+  // if the device cannot hold the cluster).
+  pl.zf_cs = pl.zf_qg = pl.zf_rmax = pl.zf_groups = pl.zf_threads = 0;
+  pl.zf_smem = 0;
+  {
+    const int req = tl ? tl->zfuse : 0;
+    std::vector<int> cands;
+    if (req > 1) cands = {req};
+    const bool direct = !pl.blue && largest_prime_factor(pl.Mf) > 7;
+    for (int cs : cands) {
+      const int rmax = (H + cs - 1) / cs;
+      if (H < 2 * cs || (long long)pl.Mf * rmax > 65536) continue;
+      const size_t sm = zf_smem_bytes<T>(W, pl.Mf, pl.blue, pl.Wh, rmax, 1, 1);
+      if (sm > 160 * 1024) continue;
+      const int elems = pl.Mf * rmax;
+      const int t = ((direct ? elems : elems / 8) + 31) / 32 * 32;
+      pl.zf_cs = cs;
+      pl.zf_qg = 1;
+      pl.zf_rmax = rmax;
+      pl.zf_groups = Q;
+      pl.zf_threads = std::max(128, std::min(512, t));
+      pl.zf_smem = sm;
+      break;
+    }
+  }
   // diagnostics
   const int cap = 152 * 16;
   const int ppb = AUX_THREADS / pl.G;  // pixels per diagnostics block
@@ -416,6 +450,7 @@ class Solver : public SolverBase {
     else { SGS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
     SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
+    if (pl.zf_cs && zfused_max_clusters<T>(pl.zf_cs, pl.zf_threads, pl.zf_smem) < 1) pl.zf_cs = 0;
     return upload_tables();
   }
 
@@ -537,6 +572,16 @@ class Solver : public SolverBase {
   // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep partials (src == nullptr)
   int z_update(const T* src, T* zout) {
     const RowArgs<T> ra = row_args(src, zout);
+    if (pl.zf_cs) {
+      ZfArgs<T> za{};
+      za.r = ra;
+      za.r.smem_tables = 1;
+      za.beta = b.beta; za.gain = b.gain; za.wfac = b.wfac; za.nwarm = b.nwarm;
+      za.CS = pl.zf_cs; za.QG = pl.zf_qg; za.RMAX = pl.zf_rmax;
+      za.mgB = div_magic(pl.zf_rmax * pl.zf_qg);
+      SGS_CUDA(launch(KIND_ZF, [&]() { return launch_zfused<T>(za, pl.zf_groups, pl.zf_threads, pl.zf_smem, st); }));
+      return SEGSALSA_OK;
+    }
     const dim3 rg(pl.nqblk, pl.H);
     SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
     ColArgs<T> ca{};
@@ -944,6 +989,7 @@ class Solver : public SolverBase {
     segsalsa_str_tiling t;
     t.tile_rows = pl.THmax; t.row_pairs = pl.QB; t.col_block = pl.CB;
     t.row_threads = pl.row_threads; t.col_rows = pl.col_rows;
+    t.zfuse = pl.zf_cs ? pl.zf_cs : 1;
     return t;
   }
 
@@ -1274,7 +1320,7 @@ static TuneKey tune_key(const segsalsa_str_params& p) {
 }
 static bool same_tiling(const segsalsa_str_tiling& a, const segsalsa_str_tiling& b) {
   return a.tile_rows == b.tile_rows && a.row_pairs == b.row_pairs && a.col_block == b.col_block &&
-         a.row_threads == b.row_threads && a.col_rows == b.col_rows;
+         a.row_threads == b.row_threads && a.col_rows == b.col_rows && a.zfuse == b.zfuse;
 }
 
 constexpr int BATCH_CHUNK = 64;         // iterations per captured graph
@@ -1620,7 +1666,7 @@ struct segsalsa_str_batch {
                                                        : sgs::make_plan<double>(&pr, pl, msg, &t);
           if (rc) return false;
           key.push_back(pl.THmax); key.push_back(pl.QB); key.push_back(pl.CB);
-          key.push_back(pl.row.threads); key.push_back(pl.NSEG);
+          key.push_back(pl.row.threads); key.push_back(pl.NSEG); key.push_back(pl.zf_cs);
         }
         return true;
       };

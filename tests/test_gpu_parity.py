@@ -45,6 +45,64 @@ def test_linear_solve(B, H, W, K, M, prec):
     assert max_abs(z, ref) <= tol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("H,W,K,M,prec,wscale", [
+    (64, 64, 4, 1, "fp64", 1.0), (145, 145, 16, 1, "fp32", 1.0), (37, 50, 5, 2, "fp32", 1.0),
+    (33, 17, 32, 1, "fp32", 1.0), (96, 131, 4, 1, "fp32", 1.0), (40, 37, 8, 1, "fp64", 5.0),
+    (71, 64, 6, 1, "fp32", 5.0), (35, 24, 3, 0, "fp64", 3.0)])
+def test_linear_solve_cluster_bands(B, H, W, K, M, prec, wscale):
+    """The z-update fused over a thread-block cluster (every cluster size that the image admits)
+    against the oracle's DFT solve and the three-launch path. wscale > 1 scales the shift
+    weights: the column recursions then decay slowly and a band's start values come from
+    several other bands, or from the whole period."""
+    om = wscale * O.gaussian_weights(M, 0.5 + 0.5 * M)
+    dt = np.float64 if prec == "fp64" else np.float32
+    rhs = synth.random_field((K, H, W), seed=H * 1000 + W + 7).astype(dt)
+    ref = O.linear_solve(rhs.astype(np.float64), om, M)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    mk = lambda zf: B.Solver(B.make_params(H, W, K, M=M, sigma=0.5 + 0.5 * M, precision=prec,
+                                           weights=om), tiling=B.make_tiling(zfuse=zf))
+    s1 = mk(1)
+    assert s1.tiling()[5] == 1
+    z1 = hwk_to_khw(s1.linear_solve(khw_to_hwk(rhs)))
+    assert max_abs(z1, ref) <= tol * np.abs(ref).max()
+    fused = 0
+    for cs in (2, 4, 8, 16):
+        if H < 2 * cs:
+            continue
+        s = mk(cs)
+        if s.tiling()[5] != cs:          # the band does not fit: three launches
+            assert s.tiling()[5] == 1
+            continue
+        fused += 1
+        s.set_profiling(True)
+        z = hwk_to_khw(s.linear_solve(khw_to_hwk(rhs)))
+        assert s.kernel_stats()["zupdate_fused"][0] == 1
+        assert max_abs(z, ref) <= tol * np.abs(ref).max(), cs
+        assert max_abs(z, z1) <= 2 * tol * np.abs(ref).max(), cs
+        s.close()
+    assert fused >= 2
+    s1.close()
+
+
+def test_solve_fused_and_three_launch_agree(B):
+    """Whole solves on a 145 x 145, K = 16 image with the z-update fused over 8-CTA clusters
+    and with the default (three launches): both reach the oracle's iterate."""
+    sc = synth.scene(145, 145, 16, S=40, gap=2.0, noise_std=1.5, wrong_frac=0.05, seed=2)
+    out = []
+    for zf in (8, 0):
+        s = B.Solver(B.make_params(145, 145, 16, M=1, sigma=0.5, lam=1.5, mu=1.0, schatten_p=1,
+                                   precision="fp32"), tiling=B.make_tiling(zfuse=zf))
+        assert s.tiling()[5] == (8 if zf == 8 else 1)
+        s.set_probs(sc.p.astype(np.float32))
+        s.solve(60)
+        out.append(s.get_z())
+        s.close()
+    ref, _ = O.solve(sc.p, 1, 0.5, 1.5, 1.0, 1, 60)
+    for z in out:
+        assert max_abs(z, ref.z) < 1e-4
+    assert max_abs(out[0], out[1]) < 1e-5
+
+
 # ------------------------------------------------ sweep (eqs. 13-14 + next rhs) alone
 
 @pytest.mark.parametrize("H,W,K,M,sp,prec", [
