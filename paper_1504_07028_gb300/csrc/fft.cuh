@@ -182,40 +182,63 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ Xin, cplx<
   }
 }
 
-// A Stockham stage of prime radix R > 7 computed output by output: output o of sequence b is
-// sum_r X[t + r nb] w^{r (j s + m nb)} with o = g Ns R + m Ns + j, t = g Ns + j, s = nb / Ns
-// (twiddle and the radix-R DFT root folded into one table index). Out of place.
+// A Stockham stage of prime radix R > 7: output o = g Ns R + m Ns + j of sequence b is
+// X_m = sum_r y_r w^(r m nb), y_r = x_{t + r nb} w^(r j s), t = g Ns + j, s = nb / Ns, w the
+// Mf-th root of unity (w^nb the R-th). The inter-stage twiddles are applied to the input in place
+// first (only when Ns > 1). Then each work item computes one pair of outputs m and R - m from
+// the symmetric and antisymmetric sums P_r = y_r + y_{R-r}, Q_r = y_r - y_{R-r}:
+//   X_m = y_0 + sum_r P_r Re(w_rm) + i sum_r Q_r Im(w_rm),  X_{R-m} = same with - i ...,
+// r = 1 .. (R-1)/2 (since w_{(R-r) m} = conj(w_rm)); m = 0 gives X_0 = y_0 + sum_r P_r alone.
+// Xin is overwritten by the twiddled input; the output goes to Xout.
 template <typename T>
-__device__ __forceinline__ void fft_direct_stage(const cplx<T>* __restrict__ Xin,
+__device__ __forceinline__ void fft_direct_stage(cplx<T>* __restrict__ Xin,
                                                  cplx<T>* __restrict__ Xout, int B, uint32_t mgB,
                                                  int Mf, int R, int Ns, uint32_t mg_ns,
                                                  uint32_t mg_nsr, const cplx<T>* tw, int S) {
   using C = cplx<T>;
+  (void)mg_nsr;
   const int nb = Mf / R;
-  const int items = Mf * B;
   const int s = nb / Ns;
-  const int NsR = Ns * R;
+  if (Ns > 1) {
+    // element n = t + r nb of sequence b gets w^(r j s), j = t mod Ns; r j s < R nb = Mf
+    for (int it = threadIdx.x; it < Mf * B; it += blockDim.x) {
+      const int n = qdiv(it, mgB), b = it - n * B;
+      const int r = n / nb, t = n - r * nb;
+      const int jj = t - qdiv(t, mg_ns) * Ns;
+      const int e = r * jj * s;
+      if (e) {
+        const int q = px(n * S + b);
+        Xin[q] = cmul(Xin[q], tw[e]);
+      }
+    }
+    __syncthreads();
+  }
+  const int hm = (R + 1) / 2;
+  const int items = nb * B * hm;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int o = qdiv(it, mgB), b = it - o * B;
-    const int g = qdiv(o, mg_nsr);
-    const int rem = o - g * NsR;
-    const int m = qdiv(rem, mg_ns);
-    const int j = rem - m * Ns;
-    const int t = g * Ns + j;
-    int step = j * s + m * nb;
-    step -= (step >= Mf) ? Mf : 0;
-    int idx = 0;
-    T ax = T(0), ay = T(0);
+    const int rest = qdiv(it, mgB), b = it - rest * B;   // sequences fastest: shared loads
+    const int t = rest / hm, m = rest - t * hm;
     const int src = t * S + b;
-    for (int r = 0; r < R; ++r) {
-      const C v = Xin[px(src + r * nb * S)];
-      const C w = tw[idx];
-      ax += v.x * w.x - v.y * w.y;
-      ay += v.x * w.y + v.y * w.x;
+    const C y0 = Xin[px(src)];
+    const int step = m * nb;                               // < Mf
+    int idx = 0;
+    T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+    for (int r = 1; r < hm; ++r) {
+      const C yr = Xin[px(src + r * nb * S)];
+      const C yq = Xin[px(src + (R - r) * nb * S)];
       idx += step;
       idx -= (idx >= Mf) ? Mf : 0;
+      const C w = tw[idx];
+      ax += (yr.x + yq.x) * w.x;
+      ay += (yr.y + yq.y) * w.x;
+      bx += (yr.x - yq.x) * w.y;
+      by += (yr.y - yq.y) * w.y;
     }
-    Xout[px(o * S + b)] = mkc<T>(ax, ay);
+    const int g = qdiv(t, mg_ns), jj = t - g * Ns;
+    const int ob = g * Ns * R + jj;
+    // i (bx + i by) = -by + i bx
+    Xout[px((ob + m * Ns) * S + b)] = mkc<T>(y0.x + ax - by, y0.y + ay + bx);
+    if (m > 0) Xout[px((ob + (R - m) * Ns) * S + b)] = mkc<T>(y0.x + ax + by, y0.y + ay - bx);
   }
 }
 
@@ -660,8 +683,8 @@ inline bool fft_smooth7(long n) {
   return n == 1;
 }
 
-// Transform length and Stockham stages of a row of length N (radices 8, 4, 2, 3, 5, 7 first,
-// then direct prime stages); false when a stage table would overflow.
+// Transform length and Stockham stages of a row of length N (direct prime stages first, then
+// radices 8, 4, 2, 3, 5, 7); false when a stage table would overflow.
 inline long largest_prime_factor(long n) {
   long best = 1;
   for (long p = 2; p * p <= n; ++p)
@@ -687,12 +710,15 @@ inline bool make_fft_plan(int N, FftPlan<T>& pl) {
     pl.radix[s] = r; pl.ns[s] = ns; pl.mg_ns[s] = div_magic(ns); pl.mg_nsr[s] = div_magic(ns * r);
     ns *= r; ++s; rest /= r;
   };
+  // prime factors above 7 first: the first stage has Ns = 1, so a direct stage there needs no
+  // inter-stage twiddles
+  for (int p = 11; p <= FFT_DIRECT_MAX; p += 2)
+    if (largest_prime_factor(p) == p)
+      while (rest % p == 0) push(p);
   while (rest % 8 == 0) push(8);
   while (rest % 4 == 0) push(4);
   while (rest % 2 == 0) push(2);
   for (int p : {3, 5, 7})
-    while (rest % p == 0) push(p);
-  for (int p = 11; rest > 1 && p <= FFT_DIRECT_MAX; p += 2)
     while (rest % p == 0) push(p);
   pl.nst = s;
   return rest == 1 && s <= FFT_MAXST;
@@ -702,11 +728,11 @@ template <typename T>
 inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_threads = 1024) {
   RowLaunch r{};
   // one radix-8 butterfly (eight values) per thread and stage; fewer threads loop. A direct
-  // prime stage (prime factor 11 .. 127) sums R terms per output in sequence: there, one
-  // thread per output keeps the chain short.
+  // prime stage (prime factor 11 .. 127) sums (R - 1) / 2 terms per pair of outputs in
+  // sequence: there, one thread per output pair keeps the chain short.
   const int elems = Mf * QB;
   const bool direct = !blue && largest_prime_factor(Mf) > 7;
-  int t = ((direct ? elems : elems / 8) + 31) / 32 * 32;
+  int t = ((direct ? elems / 2 : elems / 8) + 31) / 32 * 32;
   const int cap = std::min(target_threads, 1024);
   r.threads = t < 64 ? 64 : (t > cap ? cap : t);
   r.tables = row_smem_bytes<T>(N, Mf, blue, QB, 1) <= 160 * 1024;

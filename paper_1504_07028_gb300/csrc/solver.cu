@@ -285,7 +285,7 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
       const size_t sm = zf_smem_bytes<T>(W, pl.Mf, pl.blue, pl.Wh, rmax, 1, 1);
       if (sm > 160 * 1024) continue;
       const int elems = pl.Mf * rmax;
-      const int t = ((direct ? elems : elems / 8) + 31) / 32 * 32;
+      const int t = ((direct ? elems / 2 : elems / 8) + 31) / 32 * 32;
       pl.zf_cs = cs;
       pl.zf_qg = 1;
       pl.zf_rmax = rmax;
