@@ -104,25 +104,37 @@ __host__ __device__ constexpr double root_sin(int R, int q) {
                 : q == 5 ? -0.97492791218182360702 : -0.78183148246802980871);
 }
 
+// Output pairs m, R - m from the sums P_r = v_r + v_{R-r} and differences Q_r = v_r - v_{R-r},
+// r = 1 .. (R-1)/2 (the roots of r and R - r are conjugate):
+//   X_m = v_0 + sum_r P_r cos_rm + (sum_r Q_r.y sin_rm, -sum_r Q_r.x sin_rm),  X_{R-m} = ... -.
 template <int R, typename C> struct DftOdd {
   __device__ __forceinline__ static void run(C* v) {
     using T = decltype(v[0].x);
-    C in[R];
+    constexpr int H = (R - 1) / 2;
+    C P[H + 1], Q[H + 1];
 #pragma unroll
-    for (int r = 0; r < R; ++r) in[r] = v[r];
+    for (int r = 1; r <= H; ++r) {
+      P[r].x = v[r].x + v[R - r].x; P[r].y = v[r].y + v[R - r].y;
+      Q[r].x = v[r].x - v[R - r].x; Q[r].y = v[r].y - v[R - r].y;
+    }
+    const C v0 = v[0];
+    C x0 = v0;
 #pragma unroll
-    for (int m = 0; m < R; ++m) {
-      C acc = in[0];
+    for (int r = 1; r <= H; ++r) { x0.x += P[r].x; x0.y += P[r].y; }
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
+    for (int m = 1; m <= H; ++m) {
+      T ax = v0.x, ay = v0.y, bx = T(0), by = T(0);
+#pragma unroll
+      for (int r = 1; r <= H; ++r) {
         const int q = (r * m) % R;
         const T cr = T(root_cos(R, q)), sr = T(root_sin(R, q));
-        // in[r] * exp(-2 pi i q / R)
-        acc.x += in[r].x * cr + in[r].y * sr;
-        acc.y += in[r].y * cr - in[r].x * sr;
+        ax += P[r].x * cr; ay += P[r].y * cr;
+        bx += Q[r].y * sr; by -= Q[r].x * sr;
       }
-      v[m] = acc;
+      v[m].x = ax + bx; v[m].y = ay + by;
+      v[R - m].x = ax - bx; v[R - m].y = ay - by;
     }
+    v[0] = x0;
   }
 };
 template <typename C> struct Dft<3, C> : DftOdd<3, C> {};
