@@ -17,6 +17,13 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, int M, int G, bool diag, int til
 template <typename T>
 cudaError_t prepare_sweep(int M, int G, size_t smem, size_t smem_diag);
 
+// The same for K equal to the lane count G (compile-time class strides).
+template <typename T>
+cudaError_t launch_sweep_keq(const SweepArgs<T>& a, int M, int G, bool diag, int tiles,
+                             size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t prepare_sweep_keq(int M, int G, size_t smem, size_t smem_diag);
+
 // The same with g4 as the probability simplex indicator.
 template <typename T>
 cudaError_t launch_sweep_simplex(const SweepArgs<T>& a, int M, int G, bool diag, int tiles,
@@ -30,6 +37,12 @@ extern template cudaError_t launch_sweep_simplex<float>(const SweepArgs<float>&,
                                                         int, size_t, cudaStream_t);
 extern template cudaError_t launch_sweep_simplex<double>(const SweepArgs<double>&, int, int, bool,
                                                          int, size_t, cudaStream_t);
+extern template cudaError_t prepare_sweep_keq<float>(int, int, size_t, size_t);
+extern template cudaError_t prepare_sweep_keq<double>(int, int, size_t, size_t);
+extern template cudaError_t launch_sweep_keq<float>(const SweepArgs<float>&, int, int, bool, int,
+                                                    size_t, cudaStream_t);
+extern template cudaError_t launch_sweep_keq<double>(const SweepArgs<double>&, int, int, bool,
+                                                     int, size_t, cudaStream_t);
 extern template cudaError_t prepare_sweep<float>(int, int, size_t, size_t);
 extern template cudaError_t prepare_sweep<double>(int, int, size_t, size_t);
 extern template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, bool, int,

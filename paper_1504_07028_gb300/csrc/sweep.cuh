@@ -184,7 +184,9 @@ constexpr int sweep_min_blocks() { return (sizeof(T) == 8 || M >= 2 || DIAG) ? 2
 
 // SIMP selects the MPO of g4: false, the projection onto the affine set 1^T xi = 1 (eq. 10);
 // true, the projection onto the probability simplex (Sec. 4's description of that MPO).
-template <typename T, int M, int G, bool DIAG, bool SIMP>
+// KEQ: the class count equals the lane count G, so the class strides are compile-time constants
+// (measured 8 % fewer sweep cycles at 145 x 145, K = 16).
+template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(const SweepArgs<T> a) {
   constexpr int L = (2 * M + 1) * (2 * M + 1);
   constexpr int E = 2 * M + 2;
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
   const int x1 = (int)(((long long)(tx + 1) * a.W) / a.ntx);
   const int TH = y1 - y0, TW = x1 - x0;
   const int EH = TH + 2 * M + 1, EW = TW + 2 * M + 1;
-  const int K = a.K;
+  const int K = KEQ ? G : a.K;
   (void)EH;
   T* Pt = a.P + (size_t)tile * a.EHmax * a.EWmax * K;   // this tile's partials (tile + halo)
   T* Pt2 = DIAG ? a.P2 + (size_t)tile * a.EHmax * a.EWmax * K : nullptr;
@@ -454,72 +456,72 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
 }
 
 // Largest dynamic shared memory granted so far to each sweep variant.
-template <typename T, int M, int G, bool DIAG, bool SIMP>
+template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 struct SweepGrant {
   static size_t v;
 };
-template <typename T, int M, int G, bool DIAG, bool SIMP>
-size_t SweepGrant<T, M, G, DIAG, SIMP>::v = 0;
+template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
+size_t SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v = 0;
 
-template <typename T, int M, int G, bool DIAG, bool SIMP>
+template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 inline cudaError_t grant_sweep(size_t smem) {
-  size_t& g = SweepGrant<T, M, G, DIAG, SIMP>::v;
+  size_t& g = SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v;
   if (smem <= g) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG, SIMP>,
+  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG, SIMP, KEQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) g = smem;
   return e;
 }
 
-template <typename T, int M, int G, bool DIAG, bool SIMP>
+template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 inline cudaError_t launch_sweep_inst(const SweepArgs<T>& a, int tiles, size_t smem,
                                      cudaStream_t st) {
-  cudaError_t e = grant_sweep<T, M, G, DIAG, SIMP>(smem);
+  cudaError_t e = grant_sweep<T, M, G, DIAG, SIMP, KEQ>(smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_sweep<T, M, G, DIAG, SIMP>, dim3(tiles), dim3(256), smem, st, a);
+  return launch_pdl(k_sweep<T, M, G, DIAG, SIMP, KEQ>, dim3(tiles), dim3(256), smem, st, a);
 }
 
-template <typename T, int M, int G, bool SIMP>
+template <typename T, int M, int G, bool SIMP, bool KEQ>
 inline cudaError_t prepare_sweep_inst(size_t smem, size_t smem_diag) {
-  cudaError_t e = grant_sweep<T, M, G, false, SIMP>(smem);
+  cudaError_t e = grant_sweep<T, M, G, false, SIMP, KEQ>(smem);
   if (e != cudaSuccess) return e;
-  return grant_sweep<T, M, G, true, SIMP>(smem_diag);
+  return grant_sweep<T, M, G, true, SIMP, KEQ>(smem_diag);
 }
 
-template <typename T, int M, bool DIAG, bool SIMP>
+template <typename T, int M, bool DIAG, bool SIMP, bool KEQ>
 inline cudaError_t launch_sweep_g(const SweepArgs<T>& a, int G, int tiles, size_t smem,
                                   cudaStream_t st) {
   switch (G) {
-    case 4: return launch_sweep_inst<T, M, 4, DIAG, SIMP>(a, tiles, smem, st);
-    case 8: return launch_sweep_inst<T, M, 8, DIAG, SIMP>(a, tiles, smem, st);
-    case 16: return launch_sweep_inst<T, M, 16, DIAG, SIMP>(a, tiles, smem, st);
-    case 32: return launch_sweep_inst<T, M, 32, DIAG, SIMP>(a, tiles, smem, st);
+    case 4: return launch_sweep_inst<T, M, 4, DIAG, SIMP, KEQ>(a, tiles, smem, st);
+    case 8: return launch_sweep_inst<T, M, 8, DIAG, SIMP, KEQ>(a, tiles, smem, st);
+    case 16: return launch_sweep_inst<T, M, 16, DIAG, SIMP, KEQ>(a, tiles, smem, st);
+    case 32: return launch_sweep_inst<T, M, 32, DIAG, SIMP, KEQ>(a, tiles, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T, bool DIAG, bool SIMP>
+template <typename T, bool DIAG, bool SIMP, bool KEQ>
 inline cudaError_t launch_sweep_md(const SweepArgs<T>& a, int M, int G, int tiles, size_t smem,
                                    cudaStream_t st) {
   switch (M) {
-    case 0: return launch_sweep_g<T, 0, DIAG, SIMP>(a, G, tiles, smem, st);
-    case 1: return launch_sweep_g<T, 1, DIAG, SIMP>(a, G, tiles, smem, st);
-    case 2: return launch_sweep_g<T, 2, DIAG, SIMP>(a, G, tiles, smem, st);
+    case 0: return launch_sweep_g<T, 0, DIAG, SIMP, KEQ>(a, G, tiles, smem, st);
+    case 1: return launch_sweep_g<T, 1, DIAG, SIMP, KEQ>(a, G, tiles, smem, st);
+    case 2: return launch_sweep_g<T, 2, DIAG, SIMP, KEQ>(a, G, tiles, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
 // The instantiations of one precision and one g4 variant (each in its own translation unit).
-template <typename T, bool SIMP>
+template <typename T, bool SIMP, bool KEQ>
 inline cudaError_t launch_sweep_variant(const SweepArgs<T>& a, int M, int G, bool diag,
                                         int tiles, size_t smem, cudaStream_t st) {
-  return diag ? launch_sweep_md<T, true, SIMP>(a, M, G, tiles, smem, st)
-              : launch_sweep_md<T, false, SIMP>(a, M, G, tiles, smem, st);
+  return diag ? launch_sweep_md<T, true, SIMP, KEQ>(a, M, G, tiles, smem, st)
+              : launch_sweep_md<T, false, SIMP, KEQ>(a, M, G, tiles, smem, st);
 }
-template <typename T, bool SIMP>
+template <typename T, bool SIMP, bool KEQ>
 inline cudaError_t prepare_sweep_variant(int M, int G, size_t smem, size_t smem_diag) {
 #define SGS_PREP(MM, GG) \
-  if (M == MM && G == GG) return prepare_sweep_inst<T, MM, GG, SIMP>(smem, smem_diag);
+  if (M == MM && G == GG) return prepare_sweep_inst<T, MM, GG, SIMP, KEQ>(smem, smem_diag);
   SGS_PREP(0, 4) SGS_PREP(0, 8) SGS_PREP(0, 16) SGS_PREP(0, 32)
   SGS_PREP(1, 4) SGS_PREP(1, 8) SGS_PREP(1, 16) SGS_PREP(1, 32)
   SGS_PREP(2, 4) SGS_PREP(2, 8) SGS_PREP(2, 16) SGS_PREP(2, 32)
