@@ -71,15 +71,20 @@ __global__ void k_labels(const T* z, int n, int K, int32_t* lab) {
 
 // Euclidean projection of every pixel vector onto the probability simplex (Michelot's
 // active-set iteration: theta = (sum of the active entries - 1) / |active|, drop entries
-// <= theta, repeat; exact after at most K rounds), plus per-block partials of
-// min z, max |1^T z - 1| and sum_i -ln(p_i^T proj(z_i)). G lanes per pixel, class k on lane k.
+// <= theta, repeat; exact after at most K rounds), plus per-block partials of min z,
+// max |1^T z - 1|, sum_i -ln(p_i^T proj(z_i)) and ||G^T d||^2 (G^T d gathered from the tile
+// partials P2 in the row pass's order: covY vertical covers per row, offX per-column tile
+// offsets). G lanes per pixel, class k on lane k.
 template <typename T, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p, T* zp, int n,
-                                                        int K, double* part /*[blocks][3]*/) {
+                                                        int K, const T* P2, const int* covY,
+                                                        const int* offX, int W, int ntx,
+                                                        int EHmax, int EWmax,
+                                                        double* part /*[blocks][4]*/) {
   __shared__ double red32[32];
   constexpr int PPB = AUX_THREADS / G;
   const int g = threadIdx.x % G;
-  T vmin = T(1e30), vdev = T(0), vdata = T(0);
+  T vmin = T(1e30), vdev = T(0), vdata = T(0), vgsq = T(0);
   pdl_wait();
   for (int i0 = blockIdx.x * PPB; i0 < n; i0 += gridDim.x * PPB) {
     const int i = i0 + threadIdx.x / G;
@@ -101,18 +106,37 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
     const T q = ok ? fmax(v - theta, T(0)) : T(0);
     if (ok) zp[(size_t)i * K + g] = q;
     const T pz = group_sum<G>(pk * q);
-    if (ok) vmin = fmin(vmin, v);
+    if (ok) {
+      vmin = fmin(vmin, v);
+      const int y = i / W, x = i - y * W;
+      const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
+      const int rb0 = c0 < 0 ? -1 : (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
+      const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
+      const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
+      T gd = T(0);
+      if (rb0 >= 0) {
+        if (o0 >= 0) gd += P2[rb0 + o0 + g];
+        if (o1 >= 0) gd += P2[rb0 + o1 + g];
+      }
+      if (rb1 >= 0) {
+        if (o0 >= 0) gd += P2[rb1 + o0 + g];
+        if (o1 >= 0) gd += P2[rb1 + o1 + g];
+      }
+      vgsq += gd * gd;
+    }
     if (i < n && g == 0) {
       vdev = fmax(vdev, fabs(s - T(1)));
       vdata -= log(pz);
     }
   }
-  const double a = block_min_d((double)vmin, red32);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 0] = a;
-  const double b = block_max_d((double)vdev, red32);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = b;
-  const double c = block_sum_d((double)vdata, red32);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = c;
+  const double a = block_min_w<T>(vmin, red32);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 0] = a;
+  const double b = block_max_w<T>(vdev, red32);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 1] = b;
+  const double c = block_sum_w<T>(vdata, red32);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 2] = c;
+  const double d = block_sum_w<T>(vgsq, red32);
+  if (threadIdx.x == 0) part[4 * blockIdx.x + 3] = d;
 }
 
 // sum_i ||[J zp]_i||_{S_p} per block (zp pixel-major), via the 2x2 Gram matrix of eq. (5):
@@ -174,23 +198,27 @@ __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* ome
       val += (sp == 1) ? s1 + s2 : (sp == 2) ? sqrt(fmax(a + c, T(0))) : s1;
     }
   }
-  const double t = block_sum_d((double)val, red32);
+  const double t = block_sum_w<T>(val, red32);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 template <typename T, int G>
 inline void launch_project(int blocks, cudaStream_t st, const T* z, const T* p, T* zp, int n,
-                           int K, double* part) {
-  launch_pdl(k_project<T, G>, dim3(blocks), dim3(AUX_THREADS), 0, st, z, p, zp, n, K, part);
+                           int K, const T* P2, const int* covY, const int* offX, int W, int ntx,
+                           int EHmax, int EWmax, double* part) {
+  launch_pdl(k_project<T, G>, dim3(blocks), dim3(AUX_THREADS), 0, st, z, p, zp, n, K, P2, covY,
+             offX, W, ntx, EHmax, EWmax, part);
 }
 template <typename T>
 inline cudaError_t launch_project_g(int G, int blocks, cudaStream_t st, const T* z, const T* p,
-                                    T* zp, int n, int K, double* part) {
+                                    T* zp, int n, int K, const T* P2, const int* covY,
+                                    const int* offX, int W, int ntx, int EHmax, int EWmax,
+                                    double* part) {
   switch (G) {
-    case 4: launch_project<T, 4>(blocks, st, z, p, zp, n, K, part); break;
-    case 8: launch_project<T, 8>(blocks, st, z, p, zp, n, K, part); break;
-    case 16: launch_project<T, 16>(blocks, st, z, p, zp, n, K, part); break;
-    default: launch_project<T, 32>(blocks, st, z, p, zp, n, K, part); break;
+    case 4: launch_project<T, 4>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    case 8: launch_project<T, 8>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    case 16: launch_project<T, 16>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    default: launch_project<T, 32>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
   }
   return cudaGetLastError();
 }
@@ -215,46 +243,11 @@ inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const
   return cudaGetLastError();
 }
 
-// Sum of squares of G^T d, gathered from the tile partials P2 in the row pass's fixed order
-// (covY: vertical covers per row, offX: per-column tile offsets).
-template <typename T>
-__global__ void __launch_bounds__(AUX_THREADS) k_gather_sq(const T* P2, const int* covY,
-                                                          const int* offX, int H, int W, int K,
-                                                          int ntx, int EHmax, int EWmax,
-                                                          double* part) {
-  __shared__ double red32[32];
-  T val = T(0);
-  const size_t tot = (size_t)H * W * K;
-  pdl_wait();
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % K);
-    const size_t pix = i / K;
-    const int y = (int)(pix / W), x = (int)(pix % W);
-    const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
-    const int rb0 = c0 < 0 ? -1 : (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
-    const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
-    const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
-    T v = T(0);
-    if (rb0 >= 0) {
-      if (o0 >= 0) v += P2[rb0 + o0 + k];
-      if (o1 >= 0) v += P2[rb0 + o1 + k];
-    }
-    if (rb1 >= 0) {
-      if (o0 >= 0) v += P2[rb1 + o0 + k];
-      if (o1 >= 0) v += P2[rb1 + o1 + k];
-    }
-    val += v * v;
-  }
-  const double t = block_sum_d((double)val, red32);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
 // One trace record (k, primal, dual, objective, min z, max |1^T z - 1|), reducing the block
 // partials in a fixed order.
-__global__ void k_finalize_trace(const double* sq, int nsq, const double* gsq, int ngsq,
-                                 const double* proj, int nproj, const double* prior, int nprior,
-                                 double k, double mu, double lambda, double* rec) {
+__global__ void __launch_bounds__(AUX_THREADS) k_finalize_trace(
+    const double* sq, int nsq, const double* proj, int nproj, const double* prior, int nprior,
+    double k, double mu, double lambda, double* rec) {
   __shared__ double red32[32];
   constexpr int U = 8;  // independent loads in flight per thread
   double a = 0.0, b = 0.0, c = 0.0, d = 0.0, mn = 1e300, mx = 0.0;
@@ -276,12 +269,12 @@ __global__ void k_finalize_trace(const double* sq, int nsq, const double* gsq, i
   };
   pdl_wait();
   a = sum(sq, nsq, 1, 0);
-  b = sum(gsq, ngsq, 1, 0);
-  c = sum(proj, nproj, 3, 2);
+  b = sum(proj, nproj, 4, 3);
+  c = sum(proj, nproj, 4, 2);
   d = sum(prior, nprior, 1, 0);
   for (int i = threadIdx.x; i < nproj; i += blockDim.x) {
-    mn = fmin(mn, proj[3 * i]);
-    mx = fmax(mx, proj[3 * i + 1]);
+    mn = fmin(mn, proj[4 * i]);
+    mx = fmax(mx, proj[4 * i + 1]);
   }
   a = block_sum_d(a, red32);
   if (threadIdx.x == 0) rec[1] = sqrt(a);

@@ -165,4 +165,39 @@ __device__ __forceinline__ double block_max_d(double v, double* red32) {
   return -block_min_d(-v, red32);
 }
 
+// Block reductions of per-thread values in the working precision T: shuffles in T within each
+// warp, then thread 0 adds (or compares) the warp results in FP64 in warp order. The FP64 work is
+// one operation per warp (FP64 is a narrow pipe on this part); the order is fixed, so equal
+// inputs give equal bits. The result is valid in thread 0.
+template <typename T>
+__device__ __forceinline__ double block_sum_w(T v, double* red32) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red32[w] = (double)v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) t += red32[i];
+  return t;
+}
+template <typename T>
+__device__ __forceinline__ double block_min_w(T v, double* red32) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red32[w] = (double)v;
+  __syncthreads();
+  double t = 1e300;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) t = fmin(t, red32[i]);
+  return t;
+}
+template <typename T>
+__device__ __forceinline__ double block_max_w(T v, double* red32) {
+  return -block_min_w<T>(-v, red32);
+}
+
 }  // namespace sgs

@@ -137,7 +137,7 @@ struct Plan {
   // z-update fused over a cluster (0: three passes), its class-pair groups, threads, memory
   int zf_cs, zf_qg, zf_rmax, zf_groups, zf_threads;
   size_t zf_smem;
-  int nproj_blk, nprior_blk, ngsq_blk;
+  int nproj_blk, nprior_blk;
   std::vector<int> covY, covX;  // [H][MAXCOV], [W][MAXCOV]
 };
 
@@ -301,7 +301,6 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   // at least four grid-stride rounds per block, at most 16 blocks per SM
   pl.nproj_blk = std::max(1, std::min(cap, (pl.n + 4 * ppb - 1) / (4 * ppb)));
   pl.nprior_blk = pl.nproj_blk;
-  pl.ngsq_blk = (int)std::max<long long>(1, std::min<long long>(cap, ((long long)pl.n * K + 4 * AUX_THREADS - 1) / (4 * AUX_THREADS)));
   return SEGSALSA_OK;
 }
 
@@ -322,7 +321,7 @@ struct Buffers {
   T *p, *z, *dloc, *d2, *P, *P2, *zp, *tmp, *rhsd;
   cplx<T>* S;
   int32_t* lab;
-  double *dsq, *dproj, *dprior, *dgsq, *dtrace;
+  double *dsq, *dproj, *dprior, *dtrace;
   int* flag;
   int* err;  // set by kernels whose bounded waits gave up
   T* omega;
@@ -350,9 +349,8 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.S = c.take<cplx<T>>((size_t)pl.H * pl.Wh * pl.K);
   b.lab = c.take<int32_t>(pl.n);
   b.dsq = c.take<double>(pl.ntiles);
-  b.dproj = c.take<double>(3 * (size_t)pl.nproj_blk);
+  b.dproj = c.take<double>(4 * (size_t)pl.nproj_blk);
   b.dprior = c.take<double>(pl.nprior_blk);
-  b.dgsq = c.take<double>(pl.ngsq_blk);
   b.dtrace = c.take<double>(6 * (size_t)TRACE_CAP);
   b.flag = c.take<int>(1);
   b.err = c.take<int>(1);
@@ -612,10 +610,9 @@ class Solver : public SolverBase {
 
   int diagnostics(int k, int rec) {
     const int n = pl.n, K = pl.K;
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, b.dproj); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, (const T*)b.P2, (const int*)b.covY, (const int*)b.offX, pl.W, pl.ntx, pl.EHmax, pl.EWmax, b.dproj); }));
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_prior<T>(pl.M, pl.G, pl.nprior_blk, st, b.zp, b.omega, pl.H, pl.W, K, sp, b.dprior); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_gather_sq<T>, dim3(pl.ngsq_blk), dim3(AUX_THREADS), 0, st, (const T*)b.P2, (const int*)b.covY, (const int*)b.offX, pl.H, pl.W, K, pl.ntx, pl.EHmax, pl.EWmax, b.dgsq); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(1024), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dgsq, pl.ngsq_blk, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(AUX_THREADS), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
     return SEGSALSA_OK;
   }
 

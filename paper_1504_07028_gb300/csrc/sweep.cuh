@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
                              TH + rr, EWs, EW, K);
   }
   if constexpr (DIAG) {
-    const double t = block_sum_d((double)sq, red32);
+    const double t = block_sum_w<T>(sq, red32);
     if (threadIdx.x == 0) a.diag_sq[tile] = t;
   }
 }
