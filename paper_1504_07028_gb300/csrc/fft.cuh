@@ -601,12 +601,24 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   const int nseq = 2 * a.CB;
   const int H = a.H;
   T* Sf = reinterpret_cast<T*>(a.S);
+  // 16-byte moves when every row of the block starts on a 16-byte boundary and the block is full
+  constexpr int V = 16 / sizeof(T);
+  const bool vec = (2 * (size_t)a.C * sizeof(T)) % 16 == 0 && (nseq * sizeof(T)) % 16 == 0 &&
+                   c0 + a.CB <= a.C;
   pdl_wait();  // the spectrum comes from the row pass
-  for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
-    const int y = i / nseq, s = i % nseq;
-    const int col2 = 2 * c0 + s;
-    const bool v = col2 < 2 * a.C;
-    cp_async_zfill<sizeof(T)>(buf + i, v ? Sf + (size_t)y * 2 * a.C + col2 : Sf, v);
+  if (vec) {
+    const int per_row = nseq / V;
+    for (int i = threadIdx.x; i < H * per_row; i += blockDim.x) {
+      const int y = i / per_row, v = i - y * per_row;
+      cp_async_zfill<16>(buf + y * nseq + v * V, Sf + (size_t)y * 2 * a.C + 2 * c0 + v * V, true);
+    }
+  } else {
+    for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
+      const int y = i / nseq, s = i % nseq;
+      const int col2 = 2 * c0 + s;
+      const bool v = col2 < 2 * a.C;
+      cp_async_zfill<sizeof(T)>(buf + i, v ? Sf + (size_t)y * 2 * a.C + col2 : Sf, v);
+    }
   }
   cp_async_commit();
   cp_async_wait_all();
@@ -656,10 +668,19 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
     }
   pdl_trigger();
   __syncthreads();
-  for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
-    const int y = i / nseq, ss = i % nseq;
-    const int col2 = 2 * c0 + ss;
-    if (col2 < 2 * a.C) Sf[(size_t)y * 2 * a.C + col2] = buf[i];
+  if (vec) {
+    const int per_row = nseq / V;
+    for (int i = threadIdx.x; i < H * per_row; i += blockDim.x) {
+      const int y = i / per_row, v = i - y * per_row;
+      *reinterpret_cast<float4*>(Sf + (size_t)y * 2 * a.C + 2 * c0 + v * V) =
+          *reinterpret_cast<const float4*>(buf + y * nseq + v * V);
+    }
+  } else {
+    for (int i = threadIdx.x; i < H * nseq; i += blockDim.x) {
+      const int y = i / nseq, ss = i % nseq;
+      const int col2 = 2 * c0 + ss;
+      if (col2 < 2 * a.C) Sf[(size_t)y * 2 * a.C + col2] = buf[i];
+    }
   }
 }
 
