@@ -707,8 +707,10 @@ inline uint32_t div_magic(int d) {
 }
 
 // Largest prime factor handled by a direct Stockham stage; rows with a larger prime factor use
-// Bluestein's transform.
-constexpr int FFT_DIRECT_MAX = 127;
+// Bluestein's transform. A direct stage costs about R / 2 multiply-adds per output; measured on
+// one GB300 (z-update of 256 x W, K = 8, W = 2p), direct was faster up to p = 103 and
+// Bluestein from p = 109 (p = 127: 45.0 vs 37.9 us).
+constexpr int FFT_DIRECT_MAX = 103;
 
 inline bool fft_smooth7(long n) {
   for (long r : {2L, 3L, 5L, 7L})
@@ -732,9 +734,27 @@ inline bool make_fft_plan(int N, FftPlan<T>& pl) {
     pl.Mf = N;
     pl.blue = 0;
   } else {
-    long mm = 2L * N - 1;
-    while (!fft_smooth7(mm)) ++mm;
-    pl.Mf = (int)mm;
+    // Bluestein length: the 7-smooth length in [2N - 1, 4N] with the lowest modelled cost
+    // (length x per-stage cost; radix-8 stages move the most data per barrier), which often
+    // prefers a power of two over the shortest length (N = 202: 448 = 8 8 7 rather than
+    // 405 = 3 3 3 3 5)
+    auto cost = [](long m) {
+      double c = 0.0;
+      const long len = m;
+      for (int r : {8, 4, 2, 3, 5, 7}) {
+        const double cr = r == 8 ? 6.5 : r == 4 ? 4.0 : r == 2 ? 3.0 : r == 3 ? 5.0 : r == 5 ? 7.0 : 9.0;
+        while (m % r == 0) { c += cr + 8.0; m /= r; }
+      }
+      return c * (double)len;
+    };
+    long best = 0;
+    double bc = 0.0;
+    for (long mm = 2L * N - 1; mm <= 4L * N; ++mm) {
+      if (!fft_smooth7(mm)) continue;
+      const double c = cost(mm);
+      if (!best || c < bc) { best = mm; bc = c; }
+    }
+    pl.Mf = (int)best;
     pl.blue = 1;
   }
   int rest = pl.Mf, s = 0, ns = 1;
@@ -761,7 +781,7 @@ template <typename T>
 inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_threads = 1024) {
   RowLaunch r{};
   // one radix-8 butterfly (eight values) per thread and stage; fewer threads loop. A direct
-  // prime stage (prime factor 11 .. 127) sums (R - 1) / 2 terms per pair of outputs in
+  // prime stage (prime factor 11 .. 103) sums (R - 1) / 2 terms per pair of outputs in
   // sequence: there, one thread per output pair keeps the chain short.
   const int elems = Mf * QB;
   const bool direct = !blue && largest_prime_factor(Mf) > 7;

@@ -36,7 +36,9 @@ def B(lib):
     (256, 256, 8, 1, "fp32"), (61, 2048, 3, 1, "fp32"), (33, 17, 32, 1, "fp32"),
     # rows with two prime factors above 7 (the second direct stage twiddles its input) and
     # with a radix-7 / radix-3 tail after a direct stage
-    (40, 143, 4, 1, "fp32"), (24, 121, 3, 1, "fp64"), (18, 2 * 3 * 7 * 13, 5, 1, "fp64")])
+    (40, 143, 4, 1, "fp32"), (24, 121, 3, 1, "fp64"), (18, 2 * 3 * 7 * 13, 5, 1, "fp64"),
+    # the largest direct prime (103) and the smallest row length sent to Bluestein (127)
+    (20, 206, 4, 1, "fp64"), (30, 127, 3, 1, "fp32")])
 def test_linear_solve(B, H, W, K, M, prec):
     s = _solver(B, H, W, K, M, 0.5 + 0.5 * M, 1.0, 1.0, 1, prec)
     dt = np.float64 if prec == "fp64" else np.float32
