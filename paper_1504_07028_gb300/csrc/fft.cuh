@@ -410,6 +410,44 @@ __device__ __forceinline__ T gather_row(const T* __restrict__ P, int rb0, int rb
   return v;
 }
 
+// 16-byte vectors of the working precision (four FP32 or two FP64 classes of one pixel).
+template <typename T> struct V16Of;
+template <> struct V16Of<float> { using type = float4; };
+template <> struct V16Of<double> { using type = double2; };
+template <typename T> using v16 = typename V16Of<T>::type;
+__device__ __forceinline__ float v16_at(const float4& v, int e) {
+  return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double v16_at(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float4 v16_add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ double2 v16_add(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ v16<T> ldg16(const T* p) {
+  return __ldg(reinterpret_cast<const v16<T>*>(p));
+}
+
+// gather_row for the 16 / sizeof(T) consecutive classes k, k + 1, ... (16-byte aligned), in the
+// same summation order.
+template <typename T>
+__device__ __forceinline__ v16<T> gather_row16(const T* __restrict__ P, int rb0, int rb1,
+                                               const int* oX, int x, int k) {
+  const int o0 = oX[2 * x], o1r = oX[2 * x + 1];
+  const bool hx = o1r >= 0, hy = rb1 >= 0;
+  const int o1 = hx ? o1r : o0;
+  const int r1 = hy ? rb1 : rb0;
+  const v16<T> p00 = ldg16(P + rb0 + o0 + k), p01 = ldg16(P + rb0 + o1 + k);
+  const v16<T> p10 = ldg16(P + r1 + o0 + k), p11 = ldg16(P + r1 + o1 + k);
+  v16<T> v = p00;
+  if (hx) v = v16_add(v, p01);
+  if (hy) v = v16_add(v, p10);
+  if (hx && hy) v = v16_add(v, p11);
+  return v;
+}
+
 // P offset of the row start of vertical cover cy = (tile row << 16 | ext row), -1 if absent.
 __device__ __forceinline__ int cover_row_base_raw(int cy, int ntx, int EHmax, int EWmax, int K) {
   if (cy < 0) return -1;
@@ -434,6 +472,26 @@ template <typename T>
 __device__ inline FftTables<T> row_tables(const RowArgs<T>& a, cplx<T>* tab) {
   if (a.smem_tables) return load_tables<T>(a.pl, tab);
   return FftTables<T>{a.pl.tw, a.pl.chirp, a.pl.bhat};
+}
+
+// Two adjacent complex values as one 16-byte load (FP32) or two (FP64); src 16-byte aligned.
+__device__ __forceinline__ void load_pair(const float2* src, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double2* src, double2& a, double2& b) {
+  a = __ldg(src);
+  b = __ldg(src + 1);
+}
+
+// Two adjacent complex values as 16-byte stores (dst 16-byte aligned).
+__device__ __forceinline__ void store_pair(float2* dst, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(dst) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_pair(double2* dst, double2 a, double2 b) {
+  dst[0] = a;
+  dst[1] = b;
 }
 
 template <typename T>
@@ -464,7 +522,43 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   const int tot = N * B * 2;
   const int rb0 = a.src ? -1 : cover_row_base(a, a.covY[2 * y]);
   const int rb1 = a.src ? -1 : cover_row_base(a, a.covY[2 * y + 1]);
-  for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
+  // 16-byte reads of a pixel's classes when the CTA's classes are whole aligned vectors (a
+  // caller's dense rhs may be only element-aligned)
+  constexpr int VE = 16 / sizeof(T);
+  const bool vec = a.K % VE == 0 && (2 * B) % VE == 0 && 2 * (q0 + B) <= a.K &&
+                   (reinterpret_cast<uintptr_t>(a.src) & 15) == 0;
+  if (vec) {
+    constexpr int UV = 4;
+    const int nv = 2 * B / VE;  // vectors per pixel (a power of two)
+    const int lnv = __ffs(nv) - 1;
+    const int totv = N * nv;
+    for (int i0 = threadIdx.x; i0 < totv; i0 += UV * blockDim.x) {
+      v16<T> v[UV];
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < totv) {
+          const int x = i >> lnv, j = i & (nv - 1);
+          const int k = 2 * q0 + j * VE;
+          v[u] = a.src ? ldg16(a.src + ((size_t)y * a.W + x) * a.K + k)
+                       : gather_row16<T>(a.P, rb0, rb1, cX, x, k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < totv) {
+          const int x = i >> lnv, j = i & (nv - 1);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            const int c = j * VE + e;  // class within the CTA: pair c / 2, part c % 2
+            Xf[2 * px(x * B + (c >> 1)) + (c & 1)] = v16_at(v[u], e);
+          }
+        }
+      }
+    }
+  }
+  for (int i0 = vec ? tot : threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
     T v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -488,19 +582,25 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   __syncthreads();
   const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
   pdl_trigger();
-  // unpack the two real spectra: A = (X_k + conj X_{N-k})/2, B = (X_k - conj X_{N-k})/(2i)
-  for (int i = threadIdx.x; i < a.Wh * B * 2; i += blockDim.x) {
-    const int part = i & 1;
-    const int qq = (i >> 1) & (B - 1);
-    const int kx = (i >> 1) >> a.lgB;
-    const int k = 2 * (q0 + qq) + part;
+  // unpack the two real spectra of each pair: A = (X_k + conj X_{N-k})/2,
+  // B = (X_k - conj X_{N-k})/(2i); one thread per pair, stored together when K is even
+  for (int i = threadIdx.x; i < a.Wh * B; i += blockDim.x) {
+    const int qq = i & (B - 1);
+    const int kx = i >> a.lgB;
+    const int k = 2 * (q0 + qq);
     if (k >= a.K) continue;
     const C u = dft_out<T>(R, B, kx, qq, a.pl, tb);
     const C w = dft_out<T>(R, B, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
-    C o;
-    if (part == 0) { o.x = T(0.5) * (u.x + w.x); o.y = T(0.5) * (u.y - w.y); }
-    else           { o.x = T(0.5) * (u.y + w.y); o.y = T(0.5) * (w.x - u.x); }
-    a.S[((size_t)y * a.Wh + kx) * a.K + k] = o;
+    C oa, ob;
+    oa.x = T(0.5) * (u.x + w.x); oa.y = T(0.5) * (u.y - w.y);
+    ob.x = T(0.5) * (u.y + w.y); ob.y = T(0.5) * (w.x - u.x);
+    C* dst = a.S + ((size_t)y * a.Wh + kx) * a.K + k;
+    if ((a.K & 1) == 0) {
+      store_pair(dst, oa, ob);
+    } else {
+      dst[0] = oa;
+      if (k + 1 < a.K) dst[1] = ob;
+    }
   }
 }
 
@@ -548,8 +648,12 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
         const int ka = 2 * (q0 + qq), kb = ka + 1;
         const int ks = kx < a.Wh ? kx : N - kx;
         const C* row = a.S + ((size_t)y * a.Wh + ks) * a.K;
-        if (ka < a.K) Av[u] = row[ka];
-        if (kb < a.K) Bv[u] = row[kb];
+        if (kb < a.K && (a.K & 1) == 0) {
+          load_pair(row + ka, Av[u], Bv[u]);
+        } else {
+          if (ka < a.K) Av[u] = row[ka];
+          if (kb < a.K) Bv[u] = row[kb];
+        }
       }
     }
 #pragma unroll
@@ -568,6 +672,30 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
   pdl_trigger();
   const T inv = T(1) / T(N);
+  constexpr int VE = 16 / sizeof(T);
+  const bool vec = a.K % VE == 0 && (2 * B) % VE == 0 && 2 * (q0 + B) <= a.K &&
+                   (reinterpret_cast<uintptr_t>(a.z) & 15) == 0;  // z may be a caller's buffer
+  if (vec) {
+    // 16-byte stores of VE classes of one pixel (VE / 2 pairs)
+    const int nv = 2 * B / VE;
+    const int lnv = __ffs(nv) - 1;
+    for (int i = threadIdx.x; i < N * nv; i += blockDim.x) {
+      const int x = i >> lnv, j = i & (nv - 1);
+      T o[VE];
+#pragma unroll
+      for (int e = 0; e < VE / 2; ++e) {
+        const C v = dft_out<T>(R, B, x, j * (VE / 2) + e, a.pl, tb);  // conj(v) / N
+        o[2 * e] = v.x * inv;
+        o[2 * e + 1] = -v.y * inv;
+      }
+      T* dst = a.z + ((size_t)y * a.W + x) * a.K + 2 * q0 + j * VE;
+      if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+      else
+        *reinterpret_cast<double2*>(dst) = make_double2(o[0], o[1]);
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
     const int part = i & 1;
     const int qq = (i >> 1) & (B - 1);

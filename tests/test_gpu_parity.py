@@ -50,6 +50,33 @@ def test_linear_solve(B, H, W, K, M, prec):
     assert max_abs(z, ref) <= tol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_linear_solve_element_aligned_device_buffers(B, prec):
+    """Device rhs and z that are views one element into their buffers (aligned to the element,
+    not to 16 bytes): the transforms fall back from 16-byte accesses and the result is the same
+    as from aligned buffers."""
+    import torch
+    H, W, K = 40, 48, 16
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    rhs = synth.random_field((K, H, W), seed=31).astype(dt)
+    ref = O.linear_solve(rhs.astype(np.float64), O.gaussian_weights(1, 0.5), 1)
+    s = B.Solver(B.make_params(H, W, K, M=1, sigma=0.5, precision=prec))
+    hwk = torch.from_numpy(np.ascontiguousarray(khw_to_hwk(rhs))).cuda()
+    buf_r = torch.zeros(H * W * K + 1, dtype=tdt, device="cuda")
+    buf_z = torch.zeros(H * W * K + 1, dtype=tdt, device="cuda")
+    r1, z1 = buf_r[1:].view(H, W, K), buf_z[1:].view(H, W, K)
+    r1.copy_(hwk)
+    assert r1.data_ptr() % 16 != 0 and z1.data_ptr() % 16 != 0
+    s.linear_solve(r1, z1)
+    z0 = s.linear_solve(hwk.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z1)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    assert max_abs(hwk_to_khw(z1.cpu().numpy()), ref) <= tol * np.abs(ref).max()
+    s.close()
+
+
 @pytest.mark.parametrize("H,W,K,M,prec,wscale", [
     (64, 64, 4, 1, "fp64", 1.0), (145, 145, 16, 1, "fp32", 1.0), (37, 50, 5, 2, "fp32", 1.0),
     (33, 17, 32, 1, "fp32", 1.0), (96, 131, 4, 1, "fp32", 1.0), (40, 37, 8, 1, "fp64", 5.0),
