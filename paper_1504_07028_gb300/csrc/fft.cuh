@@ -714,6 +714,7 @@ struct ColArgs {
   int K;
   int CB;                // complex columns per CTA
   int NSEG;              // segments along y
+  int SL;                // rows per segment (segment i covers rows [i SL, min((i+1) SL, H)))
   const T* beta;         // [Wh]
   const T* gain;         // [Wh]
   const T* wfac;         // [Wh] 1 or 1/(1 - beta^H)
@@ -757,8 +758,8 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   const int kx = (c < a.C) ? c / a.K : 0;
   const T beta = a.beta[kx], gain = a.gain[kx], wf = a.wfac[kx];
   const int nw = a.nwarm[kx];
-  const int s0 = act ? (int)(((long long)seg * H) / a.NSEG) : 0;
-  const int s1 = act ? (int)(((long long)(seg + 1) * H) / a.NSEG) : 0;
+  const int s0 = act ? min(seg * a.SL, H) : 0;
+  const int s1 = act ? min(s0 + a.SL, H) : 0;
   // causal start value y_{s0-1} = sum_m beta^m r_{s0-1-m}
   T acc = T(0);
   if (act) {
@@ -832,6 +833,19 @@ inline int row_pairs_per_cta(int Mf, int Q, int rows = 1 << 30, int max_elems = 
 
 inline uint32_t div_magic(int d) {
   return d <= 1 ? 0u : (uint32_t)(((1ULL << 32) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+
+// Column segments: rows per segment at least ceil(H / nseg), rounded up to 1 modulo the number
+// of buffer rows that fill the 32 shared-memory banks, so that the segments one warp holds (32 /
+// nseq of them, at the same step) sit in different banks; and the resulting segment count.
+inline void col_segments(int H, int nseg, int nseq, int tbytes, int& SL, int& NSEG) {
+  const int words = nseq * tbytes / 4;  // 4-byte words per buffer row
+  const int q = words >= 32 ? 1 : 32 / words;
+  int sl = (H + nseg - 1) / nseg;
+  if (q > 1)
+    while (sl % q != 1) ++sl;
+  SL = sl;
+  NSEG = (H + sl - 1) / sl;
 }
 
 // Largest prime factor handled by a direct Stockham stage; rows with a larger prime factor use

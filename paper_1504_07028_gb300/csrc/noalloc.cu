@@ -181,6 +181,7 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
   ColArgs<float> ca{};
   ca.H = H; ca.C = Wh * K; ca.K = K; ca.CB = CB;
   ca.NSEG = H / 24 < 1 ? 1 : (H / 24 > 1024 / (2 * CB) ? 1024 / (2 * CB) : H / 24);
+  col_segments(H, ca.NSEG, 2 * CB, (int)sizeof(float), ca.SL, ca.NSEG);
   ca.beta = reinterpret_cast<const float*>(tb + TL.beta);
   ca.gain = reinterpret_cast<const float*>(tb + TL.gain);
   ca.wfac = reinterpret_cast<const float*>(tb + TL.wfac);

@@ -131,7 +131,7 @@ struct Plan {
   size_t sweep_smem, sweep_smem_diag;
   int Wh, Mf, blue, QB, nqblk;
   RowLaunch row;
-  int CB, NSEG, col_threads, ncolblk;
+  int CB, NSEG, SL, col_threads, ncolblk;
   int row_threads, col_rows;   // target threads of a row-pass CTA; rows per column segment
   size_t col_smem;
   // z-update fused over a cluster (0: three passes), its class-pair groups, threads, memory
@@ -266,6 +266,7 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.col_rows = large_image ? 32 : 8;
   if (tl && tl->col_rows) pl.col_rows = tl->col_rows;
   pl.NSEG = std::max(1, std::min(H / pl.col_rows, 1024 / nseq));
+  col_segments(H, pl.NSEG, nseq, (int)sizeof(T), pl.SL, pl.NSEG);
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
   // z-update in one launch, on request only (measured slower than the three passes at every
@@ -584,7 +585,7 @@ class Solver : public SolverBase {
     const dim3 rg(pl.nqblk, pl.H);
     SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
     ColArgs<T> ca{};
-    ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG;
+    ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG; ca.SL = pl.SL;
     ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
     SGS_CUDA(launch(KIND_COL, [&]() { return launch_col<T>(ca, pl.ncolblk, pl.col_threads, pl.col_smem, st); }));
     SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row<T>(false, ra, rg, pl.row, st); }));
