@@ -244,49 +244,51 @@ inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const
 }
 
 // One trace record (k, primal, dual, objective, min z, max |1^T z - 1|), reducing the block
-// partials in a fixed order.
-__global__ void __launch_bounds__(AUX_THREADS) k_finalize_trace(
+// partials in a fixed order. One warp: each lane sums a strided subset in FP64 (four independent
+// chains), then shuffles; no block barriers (the partials number a few hundred to a few
+// thousand, and FP64 is a narrow pipe on this part).
+__global__ void __launch_bounds__(32) k_finalize_trace(
     const double* sq, int nsq, const double* proj, int nproj, const double* prior, int nprior,
     double k, double mu, double lambda, double* rec) {
-  __shared__ double red32[32];
-  constexpr int U = 8;  // independent loads in flight per thread
-  double a = 0.0, b = 0.0, c = 0.0, d = 0.0, mn = 1e300, mx = 0.0;
+  const int l = threadIdx.x;
   auto sum = [&](const double* v, int n, int stride, int off) {
-    double acc[U];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i0 = l; i0 < n; i0 += 4 * 32) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = 0.0;
-    for (int i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = i0 + u * blockDim.x;
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 32 * u;
         if (i < n) acc[u] += v[stride * i + off];
       }
     }
-    double t = 0.0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) t += acc[u];
-    return t;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
   };
   pdl_wait();
-  a = sum(sq, nsq, 1, 0);
-  b = sum(proj, nproj, 4, 3);
-  c = sum(proj, nproj, 4, 2);
-  d = sum(prior, nprior, 1, 0);
-  for (int i = threadIdx.x; i < nproj; i += blockDim.x) {
+  double a = sum(sq, nsq, 1, 0);
+  double b = sum(proj, nproj, 4, 3);
+  double c = sum(proj, nproj, 4, 2);
+  double d = sum(prior, nprior, 1, 0);
+  double mn = 1e300, mx = 0.0;
+  for (int i = l; i < nproj; i += 32) {
     mn = fmin(mn, proj[4 * i]);
     mx = fmax(mx, proj[4 * i + 1]);
   }
-  a = block_sum_d(a, red32);
-  if (threadIdx.x == 0) rec[1] = sqrt(a);
-  b = block_sum_d(b, red32);
-  if (threadIdx.x == 0) rec[2] = mu * sqrt(b);
-  c = block_sum_d(c, red32);
-  d = block_sum_d(d, red32);
-  if (threadIdx.x == 0) rec[3] = c + lambda * d;
-  mn = block_min_d(mn, red32);
-  if (threadIdx.x == 0) rec[4] = mn;
-  mx = block_max_d(mx, red32);
-  if (threadIdx.x == 0) { rec[5] = mx; rec[0] = k; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (l == 0) {
+    rec[0] = k;
+    rec[1] = sqrt(a);
+    rec[2] = mu * sqrt(b);
+    rec[3] = c + lambda * d;
+    rec[4] = mn;
+    rec[5] = mx;
+  }
 }
 
 }  // namespace sgs
