@@ -17,7 +17,8 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, int M, int G, bool diag, int til
 template <typename T>
 cudaError_t prepare_sweep(int M, int G, size_t smem, size_t smem_diag);
 
-// The same for K equal to the lane count G (compile-time class strides).
+// The same for K equal to the lane count G and full-width tiles (NC = 256 / G): compile-time
+// class strides and z-tile stride.
 template <typename T>
 cudaError_t launch_sweep_keq(const SweepArgs<T>& a, int M, int G, bool diag, int tiles,
                              size_t smem, cudaStream_t st);

@@ -447,7 +447,7 @@ class Solver : public SolverBase {
     carve<T>(pl, reinterpret_cast<char*>(ws), b);
     if (pr->stream) st = reinterpret_cast<cudaStream_t>(pr->stream);
     else { SGS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
-    if (pl.K == pl.G) SGS_CUDA(prepare_sweep_keq<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
+    if (pl.K == pl.G && pl.NC == 256 / pl.G) SGS_CUDA(prepare_sweep_keq<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     else SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
     if (pl.zf_cs && zfused_max_clusters<T>(pl.zf_cs, pl.zf_threads, pl.zf_smem) < 1) pl.zf_cs = 0;
@@ -603,7 +603,7 @@ class Solver : public SolverBase {
     const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
     SGS_CUDA(launch(KIND_SWEEP, [&]() {
       if (g4 == SEGSALSA_G4_SIMPLEX) return launch_sweep_simplex<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
-      return pl.K == pl.G ? launch_sweep_keq<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st)
+      return pl.K == pl.G && pl.NC == 256 / pl.G ? launch_sweep_keq<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st)
                           : launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
     }));
     return SEGSALSA_OK;

@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
   const bool colok = c < TW;
   const bool kok = colok && g < K;
   const int x = x0 + (colok ? c : 0);
-  const int EWs = a.EWmax;
+  // KEQ instantiations run only with full-width tiles (NC = 256 / G), so their z-tile row
+  // stride is a compile-time constant too
+  const int EWs = KEQ ? 256 / G + 2 * M + 1 : a.EWmax;
 
   T accW[E][E];
   constexpr int E2 = DIAG ? E : 1;
@@ -281,6 +283,14 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     for (int s = 0; s < E2; ++s) accW2[r][s] = T(0);
   T sq = T(0);
   const T tau = a.tau, mu = a.mu;
+  // shift weights in registers for the FP32 3 x 3 patch (the 5 x 5 and FP64 variants are at
+  // their register caps)
+  constexpr bool OMR = M <= 1 && sizeof(T) == 4;
+  constexpr int LR = OMR ? L : 1;
+  T omr[LR];
+#pragma unroll
+  for (int j = 0; j < LR; ++j) omr[j] = om[j];
+  auto omega_j = [&](int j) -> T { return OMR ? omr[j < LR ? j : 0] : om[j]; };
 
   for (int r = 0; r < TH; ++r) {
     const int sidx = r & 1;
@@ -332,7 +342,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
         const T z00 = zc[(dy * EWs + dx) * G];
         const T z01 = zc[(dy * EWs + dx + 1) * G];
         const T z10 = zc[((dy + 1) * EWs + dx) * G];
-        const T w = om[j];
+        const T w = omega_j(j);
         vh[j] = w * (z01 - z00) - dv[j].x;
         vv[j] = w * (z10 - z00) - dv[j].y;
       }
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
           V2 o; o.x = nh; o.y = nv;
           d2w[(size_t)j * K] = o;
         }
-        const T w = om[j];
+        const T w = omega_j(j);
         const T wh = w * (uh + nh), wv = w * (uv + nv);
         accW[dy + M][dx + M + 1] += wh;
         accW[dy + M][dx + M] -= wh + wv;
