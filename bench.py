@@ -1,13 +1,17 @@
 """Benchmark of the SegSALSA-STR SALSA sweep on GB300 (one JSON line on stdout).
 
-Workload (default): the 145x145, K=16 scene (the shape of the paper's Indian Pines subscene,
-synthetic Voronoi labels and noisy softmax probabilities), 3x3 patch with Gaussian weights
-sigma=0.5, lambda=1.5, mu=1, 300 SALSA iterations for each Schatten p in {1, 2, inf}. One
-step = for each p: set_probs (device-resident p), 300 iterations with the residual/objective
-trace every 10 iterations, label readout. value = ADMM iterations per second (all ranks).
+Workload (default): the 2048x2048, K=16 synthetic scene (64 Voronoi seeds, logits
+3*onehot + N(0,1), softmax probabilities), 3x3 patch with Gaussian weights sigma=0.5,
+lambda=2, mu=1, Schatten p=1, 200 SALSA iterations. Its working set (about 6.5 GB) is far
+larger than L2, so the sweep's fraction of the HBM roofline means what it says. One step =
+set_probs (device-resident p), 200 iterations with the residual/objective trace every 10
+iterations, label readout. value = ADMM iterations per second (all ranks). `--workload 145x145`
+runs the 145x145, K=16 scene (the shape of the paper's Indian Pines subscene) for each
+Schatten p in {1, 2, inf}; other workloads are listed under --help.
 
 `--impl reference` times the FP64 CPU oracle (the only reference there is: the paper has no
-code) on the host cores, on a bounded sample of the same workload.
+code) on the host cores, on a bounded sample of the same workload (a 256x256 crop for images
+above 512x512, scaled to the full image by pixel count).
 """
 from __future__ import annotations
 
@@ -62,6 +66,27 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
     timed by the slowest rank."""
     return units_per_rank * world / seconds_max
+
+
+def cpu_info():
+    """Host cores this process may run on and the BLAS thread setting the oracle runs under."""
+    try:
+        host = len(os.sched_getaffinity(0))
+    except Exception:
+        host = os.cpu_count() or 1
+    blas = None
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            blas = f"{var}={os.environ[var]}"
+            break
+    if blas is None:
+        try:
+            from threadpoolctl import threadpool_info
+            n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+            blas = f"threadpoolctl: {n[0]}" if n else "unset (numpy default)"
+        except Exception:
+            blas = "unset (numpy default)"
+    return {"host_cores": host, "blas_threads": blas}
 
 
 def _peaks():
@@ -162,9 +187,12 @@ def make_workload(name):
 # -------------------------------------------------------------------- reference arm (oracle)
 
 def oracle_sample(sc, cfgs, iters_per_p):
-    """Time the FP64 oracle for `iters_per_p` iterations of each solve of the workload."""
+    """Time the FP64 oracle for `iters_per_p` iterations of each solve of the workload (on the
+    crop of `oracle_crop` for large images). Returns (full-image iterations, wall s, threads
+    used, crop scale)."""
     from oracle import segsalsa_str_oracle as O
-    p = sc.p.astype(np.float32).astype(np.float64)
+    pc, scale = oracle_crop(sc)
+    p = pc.astype(np.float32).astype(np.float64)
     t0, c0 = time.perf_counter(), time.process_time()
     n = 0
     for cfg in cfgs:
@@ -172,7 +200,30 @@ def oracle_sample(sc, cfgs, iters_per_p):
                 trace_every=10)
         n += iters_per_p
     wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-    return n, wall, max(1, round(cpu / wall)) if wall > 0 else 1
+    return n * scale, wall, (max(1, round(cpu / wall)) if wall > 0 else 1), scale
+
+
+def sample_note(sc, iters, nsolves, wall):
+    """What the oracle sample was, in words."""
+    pc, scale = oracle_crop(sc)
+    what = (f"{iters} iterations of each of the {nsolves} solves" if nsolves > 1
+            else f"{iters} iterations")
+    if scale < 1.0:
+        return (f"{what} on the top-left {pc.shape[1]}x{pc.shape[2]} crop of the {sc.H}x{sc.W} "
+                f"scene ({wall:.1f} s), scaled to the full image by pixel count (x{scale:.5f})")
+    return f"{what} of the full workload ({wall:.1f} s)"
+
+
+CROP = 256          # oracle sample side for images above 512x512
+
+
+def oracle_crop(sc):
+    """The oracle's sample of a large scene: its top-left CROP x CROP probabilities, or the
+    whole scene when it is at most 512x512. Returns (p, pixel-count scale to the full image)."""
+    if sc.H * sc.W <= 512 * 512:
+        return sc.p, 1.0
+    p = np.ascontiguousarray(sc.p[:, :CROP, :CROP])
+    return p, (CROP * CROP) / (sc.H * sc.W)
 
 
 BATCH_DESC = ("64 images, H and W uniform in [96, 512], K uniform in {4, 8, 16}, 3x3 Gaussian "
@@ -217,7 +268,7 @@ def run_reference_batch(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": BATCH_DESC, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **cpu_info()},
         "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -266,7 +317,7 @@ def run_reference_mlr(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": MLR_DESC, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **cpu_info()},
         "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -285,16 +336,16 @@ def run_reference(args, rank, world):
         return
     sc, cfgs, desc = make_workload(args.workload)
     per_p = max(1, args.ref_iters)
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 1)):
         oracle_sample(sc, cfgs, 1)
-    tot_n, tot_t, cores = 0, 0.0, 1
+    tot_n, tot_t, cores = 0.0, 0.0, 1
     for _ in range(args.steps):
-        n, t, cores = oracle_sample(sc, cfgs, per_p)
+        n, t, cores, _ = oracle_sample(sc, cfgs, per_p)
         tot_n += n
         tot_t += t
     v = tot_n / tot_t
-    sample = (f"{per_p} iterations per Schatten p per step ({tot_n} iterations in {args.steps} "
-              f"steps) of the full workload")
+    sample = (sample_note(sc, per_p, len(cfgs), tot_t / max(1, args.steps)) +
+              f"; per step, {args.steps} steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ADMM iter/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -302,7 +353,7 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **cpu_info()},
         "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -334,6 +385,9 @@ def run_ours(args, rank, world, local_rank):
     p_dev = torch.from_numpy(sc.p.astype(np.float32)).to(dev)          # (K, H, W)
     labs_dev = [torch.empty((H, W), dtype=torch.int32, device=dev) for _ in cfgs]
     iters_per_step = sum(cfg.iters for cfg in cfgs)
+    ws_bytes = B.segsalsa_str_workspace_bytes(B.make_params(
+        H, W, K, M=cfgs[0].M, sigma=cfgs[0].sigma, lam=cfgs[0].lam, mu=cfgs[0].mu,
+        schatten_p=cfgs[0].schatten_p, precision="fp32"))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     pool = ThreadPoolExecutor(max_workers=len(cfgs))
 
@@ -499,9 +553,11 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         it = max(1, args.cpu_iters)
-        nn, wall, cores = oracle_sample(sc, cfgs[:1], it)
+        nn, wall, cores, _ = oracle_sample(sc, cfgs[:1], it)
         cpu = {"value": nn / wall, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
-               "sample": f"{nn} iterations of the p=1 solve of the same workload ({wall:.1f} s)"}
+               "sample": sample_note(sc, it, 1, wall) +
+                         (" (the p=1 solve)" if len(cfgs) > 1 else ""),
+               **cpu_info()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
@@ -511,8 +567,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": desc, "H": H, "W": W, "K": K, "iters_per_step": iters_per_step,
                    "concurrency": f"{len(cfgs)} independent solves per step, one stream and host "
                                   "thread each",
-                   "l2": "flushed between timed steps (256 MB write); the 145x145 working set "
-                         "(~45 MB) is L2-resident within a step",
+                   "l2": ("flushed between timed steps (256 MB write); the "
+                          f"{ws_bytes / 1e6:.0f} MB working set per solve "
+                          + ("exceeds L2" if ws_bytes > 129e6 else "is L2-resident within a step")),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "mpixel_class_iter_per_s": mpix,
         "accuracy": {"max_abs_z_vs_fp64": err, "labels_match_off_1e-3_margin": lab_ok},
@@ -675,7 +732,8 @@ def run_batch(args, rank, world, local_rank):
         v = u / wall / np.mean(units)
         cpu = {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
                "sample": f"{max(1, args.cpu_iters // 2)} iterations of two batch images "
-                         f"({wall:.1f} s), converted to iterations of the batch's mean image"}
+                         f"({wall:.1f} s), converted to iterations of the batch's mean image",
+               **cpu_info()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
@@ -832,7 +890,8 @@ def run_mlr(args, rank, world, local_rank):
         v_cpu, wall, cores = oracle_mlr_sample(it)
         cpu = {"value": v_cpu, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
                "sample": f"MLR probabilities + {it} iterations of a {MLR_CROP[0]}x{MLR_CROP[1]} "
-                         f"crop ({wall:.1f} s), scaled to the full image by pixel count"}
+                         f"crop ({wall:.1f} s), scaled to the full image by pixel count",
+               **cpu_info()}
     line = {
         "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -1007,7 +1066,8 @@ def run_diff(args, rank, world, local_rank):
         v, wall, cores = oracle_grad_sample()
         cpu = {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
                "sample": f"reference gradient (FP64 autograd through the oracle iteration) of a "
-                         f"64x64 crop, 50 iterations ({wall:.1f} s), scaled by pixel count"}
+                         f"64x64 crop, 50 iterations ({wall:.1f} s), scaled by pixel count",
+               **cpu_info()}
     line = {
         "metric": METRIC, "value": value, "unit": "ADMM iter/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -1059,7 +1119,7 @@ def run_reference_diff(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": DIFF_DESC, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "ADMM iter/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **cpu_info()},
         "e2e": {"value": v, "unit": "ADMM iter/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -1070,13 +1130,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="145x145",
-                    help="145x145 (default), 64x64, 2048x2048, HxW (K=16 synthetic scene), patchsweep, or "
+    ap.add_argument("--workload", default="2048x2048",
+                    help="2048x2048 (default), 145x145, 64x64, HxW (K=16 synthetic scene), patchsweep, or "
                          "batch64 (64 uneven images in one batch), mlr610x340 (MLR front end), or diff256 "
                          "(differentiable solver)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tilings")
     ap.add_argument("--tune-iters", type=int, default=4, help="batch64: iterations per trial")
-    ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64-check", action="store_true")

@@ -17,7 +17,7 @@ Notation (Sec. 2-4):
   G       stacking [I; J; I; I] (eq. 9, 11); u = (u1, u2, u3, u4), d likewise
   g1..g4  -ln(p^T .), lambda*||.||_{S_p}, i_+, i_1(1^T .)  (eq. 10)
 
-Readings where the paper is silent or ambiguous (each one is listed in the design doc):
+Readings where the paper is silent or ambiguous:
   * shift weights omega_j = sqrt(g_j), g_j a normalised Gaussian exp(-|s_j|^2 / (2 sigma^2))
     so that J^T J is a Gaussian-weighted structure tensor and sum omega_j^2 = 1 (Sec. 3);
   * periodic boundaries and forward differences (the "cyclic convolutions" of Sec. 4);

@@ -8,7 +8,7 @@ import tests.test_oracle_pins as P
 
 _orig = {name: getattr(O, name) for name in
          ("shift", "prox_g1", "prox_g2", "linear_solve", "prox_g4", "D_v_T", "jacobian",
-          "mlr_probs", "proj_simplex")}
+          "mlr_probs", "proj_simplex", "schatten_norms")}
 
 
 def _wrong_shift(f, s):                     # shift sign flipped
@@ -63,6 +63,16 @@ def _wrong_affine_for_simplex(v):           # the affine projection where the si
     return v - (np.sum(v, axis=0, keepdims=True) - 1.0) / v.shape[0]
 
 
+def _dropped_root(Jz, sp):                   # sum of s^p without the 1/p root
+    s = np.linalg.svd(O.jacobian_matrices(Jz), compute_uv=False)
+    return s.max(axis=-1) if sp == np.inf else np.sum(s ** sp, axis=-1)
+
+
+def _sum_for_max(Jz, sp):                   # S_inf as the sum of the singular values
+    s = np.linalg.svd(O.jacobian_matrices(Jz), compute_uv=False)
+    return s.sum(axis=-1) if sp == np.inf else _orig["schatten_norms"](Jz, sp)
+
+
 MUTATIONS = [
     ("shift", _wrong_shift, [P.test_jacobian_brute_force_loops]),
     ("prox_g1", _wrong_root, [P.test_prox_g1_stationarity]),
@@ -77,6 +87,11 @@ MUTATIONS = [
     ("mlr_probs", _dropped_bias, [P.test_mlr_brute_force]),
     ("proj_simplex", _wrong_affine_for_simplex, [P.test_simplex_g4_variant_u4_on_simplex]),
     ("mlr_probs", _wrong_softmax_axis, [P.test_mlr_brute_force, P.test_mlr_special_cases]),
+    ("schatten_norms", _dropped_root, [lambda: P.test_schatten_norms_closed_form(2),
+                                       lambda: P.test_objective_closed_form(2),
+                                       lambda: P.test_schatten_norms_from_gram_eigenvalues(2)]),
+    ("schatten_norms", _sum_for_max, [lambda: P.test_schatten_norms_closed_form(np.inf),
+                                      lambda: P.test_objective_closed_form(np.inf)]),
 ]
 
 

@@ -324,19 +324,89 @@ def test_residuals_decay_and_feasibility():
     assert obj[-1] < obj[0]
 
 
-def test_fixed_point_is_a_minimiser():
+@pytest.mark.parametrize("sp", [1, 2, np.inf])
+def test_fixed_point_is_a_minimiser(sp):
     """After many iterations z minimises (7) over the simplex: random feasible
     perturbations never lower the objective (convexity makes this a global check)."""
     sc = synth.scene(8, 8, 3, S=3, gap=1.5, noise_std=1.0, wrong_frac=0.0, seed=37)
     om = O.gaussian_weights(1, 0.5)
-    st, _ = O.solve(sc.p, 1, 0.5, 0.8, 1.0, 1, 3000)
+    st, _ = O.solve(sc.p, 1, 0.5, 0.8, 1.0, sp, 3000)
     z = O.proj_simplex(st.z)
-    f0 = O.objective(z, sc.p, 0.8, om, 1, 1)
+    f0 = O.objective(z, sc.p, 0.8, om, 1, sp)
     rng = np.random.default_rng(38)
     for eps in (1e-2, 1e-3):
         for _ in range(40):
             zq = O.proj_simplex(z + eps * rng.normal(size=z.shape))
-            assert O.objective(zq, sc.p, 0.8, om, 1, 1) >= f0 - 1e-6
+            assert O.objective(zq, sc.p, 0.8, om, 1, sp) >= f0 - 1e-6
+
+
+# ------------------------------------------- eq. (7): Schatten norms and the objective
+
+def _corner_field():
+    """4x5 image, K = 3: class 0 everywhere except pixel (0, 1) (class 1) and pixel (1, 0)
+    (class 2). With M = 0 (one shift, omega = 1) the Jacobian of a pixel is the K x 2 matrix
+    [D_h z, D_v z] (Sec. 3, eq. 4 reduces to the plain forward differences). By hand:
+      (0, 0): [e1 - e0, e2 - e0], Gram [[2, 1], [1, 2]], eigenvalues 3 and 1, so singular
+              values sqrt(3) and 1;
+      (0, 1): [e0 - e1, e0 - e1] and (1, 0): [e0 - e2, e0 - e2], rank one, singular value 2;
+      (3, 1): [0, e1 - e0] and (1, 4): [e2 - e0, 0] (periodic neighbours), singular value
+              sqrt(2);
+      every other pixel: zero."""
+    z = np.zeros((3, 4, 5))
+    z[0] = 1.0
+    z[:, 0, 1] = (0.0, 1.0, 0.0)
+    z[:, 1, 0] = (0.0, 0.0, 1.0)
+    return z
+
+
+def _corner_norms(sp):
+    r3, r2 = np.sqrt(3.0), np.sqrt(2.0)
+    n = np.zeros((4, 5))
+    n[0, 0] = {1: 1.0 + r3, 2: 2.0, np.inf: r3}[sp]
+    n[0, 1] = n[1, 0] = 2.0
+    n[3, 1] = n[1, 4] = r2
+    return n
+
+
+@pytest.mark.parametrize("sp", [1, 2, np.inf])
+def test_schatten_norms_closed_form(sp):
+    """The Schatten-p norms (Sec. 3) of hand-computed Jacobians: S_1 = s1 + s2,
+    S_2 = sqrt(s1^2 + s2^2), S_inf = s1; a rank-one matrix has every norm equal to its
+    Frobenius norm."""
+    z = _corner_field()
+    n = O.schatten_norms(O.jacobian(z, np.ones(1), 0), sp).reshape(4, 5)
+    assert np.abs(n - _corner_norms(sp)).max() < 1e-13
+
+
+@pytest.mark.parametrize("sp", [1, 2, np.inf])
+def test_objective_closed_form(sp):
+    """Eq. (7) on the hand-computed field with uniform p = 1/3: every z_i is a vertex of the
+    simplex, so p_i^T z_i = 1/3 and the data term is n ln 3; the prior is lambda times the
+    sum of the norms above."""
+    z = _corner_field()
+    p = np.full_like(z, 1.0 / 3.0)
+    lam = 0.7
+    ref = 20 * np.log(3.0) + lam * _corner_norms(sp).sum()
+    assert abs(O.objective(z, p, lam, np.ones(1), 0, sp) - ref) < 1e-12
+
+
+@pytest.mark.parametrize("sp", [1, 2, np.inf])
+def test_schatten_norms_from_gram_eigenvalues(sp):
+    """Any patch size: the singular values of [Jz]_i are the square roots of the eigenvalues
+    of its 2 x 2 Gram matrix (eq. 5), which have the closed form tr/2 +- sqrt((a-c)^2/4 + b^2)
+    (no SVD); the norms built from them match."""
+    sc = synth.scene(9, 7, 4, S=3, gap=1.0, noise_std=1.0, wrong_frac=0.0, seed=39)
+    om = O.gaussian_weights(2, 1.0)
+    Jz = O.jacobian(sc.p, om, 2)
+    h, v = Jz[:, :, 0], Jz[:, :, 1]
+    a = np.sum(h * h, axis=(0, 1)).ravel()
+    b = np.sum(h * v, axis=(0, 1)).ravel()
+    c = np.sum(v * v, axis=(0, 1)).ravel()
+    r = np.sqrt(0.25 * (a - c) ** 2 + b * b)
+    s1 = np.sqrt(0.5 * (a + c) + r)
+    s2 = np.sqrt(np.maximum(0.5 * (a + c) - r, 0.0))
+    ref = {1: s1 + s2, 2: np.sqrt(a + c), np.inf: s1}[sp]
+    assert np.allclose(O.schatten_norms(Jz, sp), ref, rtol=1e-12, atol=1e-12)
 
 
 # ------------------------------------------------------------- Sec. 5: MLR class model
