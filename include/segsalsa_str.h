@@ -56,7 +56,7 @@ typedef enum {
   SEGSALSA_ERR_OOM = -2,     /* device allocation failed or workspace too small */
   SEGSALSA_ERR_CUDA = -3,    /* a CUDA runtime call failed; the message names it */
   SEGSALSA_ERR_NUMERIC = -4, /* non-finite values appeared in the iterates */
-  SEGSALSA_ERR_TIMEOUT = -5, /* reserved for bounded device-side waits */
+  SEGSALSA_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up (see set_wait_budget) */
   SEGSALSA_ERR_STATE = -6    /* call out of order (e.g. solve before set_probs) */
 } segsalsa_status;
 
@@ -122,6 +122,19 @@ int segsalsa_str_solve(segsalsa_str_t* h, int32_t iters, double* trace, int32_t 
 int segsalsa_str_solve_until(segsalsa_str_t* h, int32_t max_iters, double tol_primal,
                              double tol_dual, int32_t check_every, int32_t* iters_done,
                              double* last_record);
+
+/* Bounded device-side waits. The kernels that wait for their own bulk copies (the sweep and
+ * the MLR class model) or for the tensor core give up after `cycles` SM clock cycles (default
+ * 2e9, about one second), set the handle's error flag, wait once more with the same limit for
+ * their copies in flight, release any tensor memory and return; the call then reports
+ * SEGSALSA_ERR_TIMEOUT and the CUDA context stays usable. This is a host-side control, not part
+ * of the method (the paper has no counterpart). With probe = 1 the next launches arm their
+ * first bulk-copy barrier with 16 bytes that no copy delivers, so that those waits run out by
+ * construction: a test of the error path that faults and hangs nothing. After a timeout in
+ * solve the iterates are undefined (call set_probs or set_state); a timeout in set_spectra
+ * keeps the previous p. Drops the handle's captured graphs. SEGSALSA_ERR_ARG if cycles < 1 or
+ * probe is not 0 or 1. */
+int segsalsa_str_set_wait_budget(segsalsa_str_t* h, int64_t cycles, int32_t probe);
 
 /* Which set g4 indicates (eqs. 10-11). SEGSALSA_G4_AFFINE (the default): the affine set
  * {1^T xi = 1} as eq. (10) defines g4, whose MPO is the affine projection. SEGSALSA_G4_SIMPLEX:
@@ -218,13 +231,18 @@ int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t o
  *    loading the library holds until exit. Limits: H*(W/2+1)*K <= 2097152, W <= 8192 when W has
  *    no prime factor above 7 and W <= 4096 otherwise, H <= 3200, 2 <= H, W, 1 <= K <= 32.
  *    Sizes beyond them return SEGSALSA_ERR_OOM; other bad arguments SEGSALSA_ERR_ARG.
- *  - No cudaMalloc / cudaFree or other device allocation happens in any call. The first call on
- *    a device looks up the array's device address and builds the tables (make it before any
- *    stream capture); later calls rebuild the tables only when H, W or c_omega change.
- *  - Runs asynchronously on `stream` (cudaStream_t, NULL = legacy default stream). Every call
- *    shares the one array, so calls that overlap on the GPU (other streams, other threads)
- *    race; nothing in it needs to start at zero, because each call writes every spectrum entry
- *    it reads. Not thread-safe. No message is stored: the status code is the error report. */
+ *  - No cudaMalloc / cudaFree or other device allocation happens in any call. Every call looks
+ *    up the array's device address in the current context (cudaGetSymbolAddress, which
+ *    allocates nothing). The first call on a device, and the first call after H, W or c_omega
+ *    change or after the device was reset (a new context), builds the tables with two small
+ *    kernels on `stream` before the solve; make the first call before any stream capture.
+ *  - Runs asynchronously on `stream` (cudaStream_t, NULL = legacy default stream). Calls on one
+ *    stream may follow each other with any geometries and no synchronisation in between. Every
+ *    call shares the one array, so calls that overlap on the GPU (different streams, other
+ *    threads) race; nothing in it needs to start at zero, because each call writes every
+ *    spectrum entry it reads. The host-side bookkeeping is locked, but concurrent calls are
+ *    still unsupported for that reason. No message is stored: the status code is the error
+ *    report. */
 int segsalsa_str_linear_solve_static(const float* rhs, float* z, int32_t H, int32_t W, int32_t K,
                                      double c_omega, void* stream);
 

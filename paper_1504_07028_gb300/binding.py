@@ -44,7 +44,7 @@ SYMBOLS = (
     "segsalsa_str_batch_destroy", "segsalsa_str_batch_last_error",
     "segsalsa_str_set_spectra", "segsalsa_str_get_probs", "segsalsa_str_solve_until",
     "segsalsa_str_set_g4", "segsalsa_str_set_log_probs", "segsalsa_str_set_lambda",
-    "segsalsa_str_set_weights", "segsalsa_str_backward",
+    "segsalsa_str_set_weights", "segsalsa_str_backward", "segsalsa_str_set_wait_budget",
 )
 
 
@@ -131,6 +131,7 @@ def load(path: str | None = None):
         "segsalsa_str_set_spectra": (C.c_int, [vp, vp, vp, vp, i32, i32]),
         "segsalsa_str_get_probs": (C.c_int, [vp, vp, i32, i32]),
         "segsalsa_str_set_g4": (C.c_int, [vp, i32]),
+        "segsalsa_str_set_wait_budget": (C.c_int, [vp, C.c_int64, i32]),
         "segsalsa_str_set_log_probs": (C.c_int, [vp, vp, i32, i32]),
         "segsalsa_str_set_lambda": (C.c_int, [vp, C.c_double]),
         "segsalsa_str_set_weights": (C.c_int, [vp, C.POINTER(C.c_double)]),
@@ -380,6 +381,11 @@ class Solver:
         return out, glam.value, np.array(gom[:], dtype=np.float64)
 
     # segsalsa_str_set_g4
+    def set_wait_budget(self, cycles: int, probe: bool = False):
+        """Clock-cycle limit of the bounded device-side waits; probe=True makes the next
+        bulk-copy waits run out (a test of the timeout path)."""
+        self._c(self.lib.segsalsa_str_set_wait_budget(self.h, int(cycles), int(probe)))
+
     def set_g4(self, mode):
         m = {"affine": SEGSALSA_G4_AFFINE, "simplex": SEGSALSA_G4_SIMPLEX}.get(mode, mode)
         self._c(self.lib.segsalsa_str_set_g4(self.h, int(m)))

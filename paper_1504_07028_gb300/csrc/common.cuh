@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace sgs {
 
 template <typename T> struct CplxOf;
@@ -119,6 +121,54 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Identity of the calling thread's current CUDA context: unique for the life of the process, so
+// it changes when a device is reset and its primary context is created anew. 0 when it cannot
+// be read (no current context, or a driver without cuCtxGetId).
+inline unsigned long long current_context_id() {
+  using Fn = int (*)(void*, unsigned long long*);  // CUresult cuCtxGetId(CUcontext, id*)
+  static const Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<Fn>(f);
+  }();
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != 0) return 0;
+  return id;
+}
+
+// Dynamic shared memory granted to one kernel, per device and per context: the attribute set
+// by cudaFuncSetAttribute belongs to the current device's context, so a second GPU (or a
+// context created after a device reset) starts from nothing.
+constexpr int kMaxDevices = 64;
+struct SmemGrants {
+  std::mutex mu;
+  unsigned long long ctx[kMaxDevices] = {};
+  size_t bytes[kMaxDevices] = {};
+};
+
+// Raise `kern`'s dynamic shared-memory limit on the current device to at least `smem`.
+template <typename K>
+inline cudaError_t grant_smem(K kern, size_t smem, SmemGrants& g) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long ctx = current_context_id();
+  std::lock_guard<std::mutex> lk(g.mu);
+  if (g.ctx[dev] != ctx) {
+    g.ctx[dev] = ctx;
+    g.bytes[dev] = 0;
+  }
+  if (smem <= g.bytes[dev] && ctx != 0) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && smem > g.bytes[dev]) g.bytes[dev] = smem;
+  return e;
 }
 
 __host__ __device__ __forceinline__ int wrap_idx(int v, int n) {

@@ -943,19 +943,14 @@ inline RowLaunch row_launch_config(int N, int Mf, int blue, int QB, int target_t
   return r;
 }
 
-template <typename K>
-inline cudaError_t grant_smem(K kern, size_t smem, size_t& granted) {
-  if (smem <= granted) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) granted = smem;
-  return e;
-}
-
 // Launchers of the row and column passes: defined (and instantiated for float and double) in
-// fft_f32.cu / fft_f64.cu so that the many kernel variants compile in parallel.
+// fft_f32.cu / fft_f64.cu so that the many kernel variants compile in parallel. With
+// pdl = false the row pass is an ordinary launch: it starts only after the previous kernel in
+// the stream has completed (needed when that kernel wrote the transform tables, which the row
+// pass copies before its programmatic-dependency wait).
 template <typename T>
 cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLaunch& rl,
-                       cudaStream_t st);
+                       cudaStream_t st, bool pdl = true);
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem, cudaStream_t st);
 // Grant the dynamic shared memory of the row / column kernels of a plan before any launch.
@@ -966,15 +961,15 @@ cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem);
 #ifdef SGS_FFT_INSTANTIATE
 template <typename T>
 struct RowGrant {
-  static size_t f, i;
+  static SmemGrants f, i;
 };
-template <typename T> size_t RowGrant<T>::f = 0;
-template <typename T> size_t RowGrant<T>::i = 0;
+template <typename T> SmemGrants RowGrant<T>::f;
+template <typename T> SmemGrants RowGrant<T>::i;
 template <typename T>
 struct ColGrant {
-  static size_t g;
+  static SmemGrants g;
 };
-template <typename T> size_t ColGrant<T>::g = 0;
+template <typename T> SmemGrants ColGrant<T>::g;
 
 template <typename T>
 cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem) {
@@ -986,13 +981,21 @@ cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem) {
 
 template <typename T>
 cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLaunch& rl,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool pdl) {
   cudaError_t e;
   if (forward) {
     if ((e = grant_smem(k_row_forward<T>, rl.smem, RowGrant<T>::f)) != cudaSuccess) return e;
+    if (!pdl) {
+      k_row_forward<T><<<grid, rl.threads, rl.smem, st>>>(a);
+      return cudaGetLastError();
+    }
     return launch_pdl(k_row_forward<T>, grid, dim3(rl.threads), rl.smem, st, a);
   }
   if ((e = grant_smem(k_row_inverse<T>, rl.smem, RowGrant<T>::i)) != cudaSuccess) return e;
+  if (!pdl) {
+    k_row_inverse<T><<<grid, rl.threads, rl.smem, st>>>(a);
+    return cudaGetLastError();
+  }
   return launch_pdl(k_row_inverse<T>, grid, dim3(rl.threads), rl.smem, st, a);
 }
 
@@ -1005,8 +1008,8 @@ cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem
 }
 
 #else
-extern template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
-extern template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t);
+extern template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t, bool);
+extern template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t, bool);
 extern template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
 extern template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
 extern template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);

@@ -3,7 +3,7 @@
 #include "zfused.cuh"
 
 namespace sgs {
-template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t);
+template cudaError_t launch_row<float>(bool, const RowArgs<float>&, dim3, const RowLaunch&, cudaStream_t, bool);
 template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
 template cudaError_t launch_zfused<float>(const ZfArgs<float>&, int, int, size_t, cudaStream_t);

@@ -3,7 +3,7 @@
 #include "zfused.cuh"
 
 namespace sgs {
-template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t);
+template cudaError_t launch_row<double>(bool, const RowArgs<double>&, dim3, const RowLaunch&, cudaStream_t, bool);
 template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
 template cudaError_t prepare_fft<double>(const RowLaunch&, size_t);
 template cudaError_t launch_zfused<double>(const ZfArgs<double>&, int, int, size_t, cudaStream_t);

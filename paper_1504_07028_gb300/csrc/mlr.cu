@@ -5,19 +5,15 @@ namespace sgs {
 
 template <typename T>
 struct MlrGrant {
-  static size_t g;
+  static SmemGrants g;
 };
-template <typename T> size_t MlrGrant<T>::g = 0;
+template <typename T> SmemGrants MlrGrant<T>::g;
 
 template <typename T>
 cudaError_t launch_mlr(const MlrArgs& a, cudaStream_t st) {
   const size_t smem = mlr_smem_bytes(a.d, a.dpad, a.npad, a.K);
-  if (smem > MlrGrant<T>::g) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_mlr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    MlrGrant<T>::g = smem;
-  }
+  const cudaError_t e = grant_smem(k_mlr<T>, smem, MlrGrant<T>::g);
+  if (e != cudaSuccess) return e;
   const int grid = (a.n + MLR_TILE - 1) / MLR_TILE;
   k_mlr<T><<<grid, MLR_THREADS, smem, st>>>(a);
   return cudaGetLastError();

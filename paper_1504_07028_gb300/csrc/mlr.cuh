@@ -27,6 +27,8 @@ struct MlrArgs {
   void* p;             // [n][K] output in the handle's precision
   int* err;            // set when a bounded wait gives up
   int n, d, dpad, K, npad;
+  long long budget;    // clock cycles a bounded wait may take
+  uint32_t probe;      // extra bytes armed on the staging barrier (0; 16 in the wait test)
 };
 
 // Byte offset of element (r, k) in a K-major, no-swizzle operand tile with kc = dpad / 8
@@ -170,13 +172,18 @@ __global__ void __launch_bounds__(MLR_THREADS) k_mlr(const MlrArgs a) {
     mbar_init(bar, 1);
     mbar_init(lbar, 1);
     mbar_fence_init();
-    mbar_arrive_expect_tx(lbar, (bytesA & ~15u) + (bytesB & ~15u));
+    mbar_arrive_expect_tx(lbar, (bytesA & ~15u) + (bytesB & ~15u) + a.probe);
   }
   mlr_stage_run(stA, srcA, bytesA, lbar);
   mlr_stage_run(stB, srcB, bytesB, lbar);
   __syncthreads();                                // barrier init and the tail bytes
-  const bool staged = mbar_wait_bounded(lbar, 0, WAIT_BUDGET_CYCLES);
-  if (!staged && threadIdx.x == 0) atomicExch(a.err, 1);
+  const bool staged = mbar_wait_bounded(lbar, 0, a.budget);
+  if (!staged) {
+    // report, and give the staging copies in flight a second bounded chance to land before
+    // the buffers are overwritten below (the tile is then computed from zeros and discarded)
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    mbar_wait_bounded(lbar, 0, a.budget);
+  }
   mlr_pack_row(As, stA, threadIdx.x, staged ? rows : 0, a.d, kc);
   if (threadIdx.x < a.npad) mlr_pack_row(Bs, stB, threadIdx.x, staged ? a.K : 0, a.d, kc);
   fence_proxy_async_smem();
@@ -196,11 +203,14 @@ __global__ void __launch_bounds__(MLR_THREADS) k_mlr(const MlrArgs a) {
     }
     tc_commit(bar);
   }
-  const bool ok = mbar_wait_bounded(bar, 0, WAIT_BUDGET_CYCLES);
+  const bool ok = mbar_wait_bounded(bar, 0, a.budget);
   tc_fence_after();
   if (!ok) {
+    // report, and give the MMA a second bounded chance to finish. A CTA has to release its
+    // tensor memory before it exits, so it is freed below either way; the error flag marks
+    // the launch's output as invalid (the call returns SEGSALSA_ERR_TIMEOUT and keeps p)
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    mbar_wait_bounded(bar, 0, WAIT_BUDGET_CYCLES);   // give the MMA a second bounded chance
+    mbar_wait_bounded(bar, 0, a.budget);
   } else {
     // epilogue: thread (warp w, lane l) holds the logits of tile row 32w + l
     float lg[32];

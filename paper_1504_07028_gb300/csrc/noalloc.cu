@@ -11,11 +11,15 @@
 // The kernels are the library's own row-DFT and column-solve passes; only the memory they
 // work in differs. Host code never dereferences g_static_scratch: the array's name on the
 // host is a stand-in, not a device address, so its device address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and cached.
+// cudaGetSymbolAddress on every call (with the caller's device current; the lookup allocates
+// nothing). The transform tables kept in the array are rebuilt whenever the geometry, the
+// device address or the CUDA context changes (a device reset reloads the module with the
+// array zeroed).
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/segsalsa_str.h"
 #include "fft.cuh"
@@ -26,16 +30,18 @@ namespace {
 constexpr size_t kSpecMaxComplex = size_t(2) << 20;                 // 2 Mi complex = 16 MiB
 constexpr size_t kSpecBytes = kSpecMaxComplex * sizeof(float2);
 constexpr size_t kTableBytes = size_t(512) << 10;                   // 512 KiB of tables
-constexpr int kMaxDev = 64;
+constexpr int kMaxDev = kMaxDevices;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kSpecBytes + kTableBytes];
 
 struct DevCache {
   unsigned char* base = nullptr;  // device address of g_static_scratch on this device
+  unsigned long long ctx = 0;     // context the tables were built in
   int H = -1, W = -1;             // geometry whose tables are in the array
   double c = -1.0;
 };
 static DevCache g_cache[kMaxDev];
+static std::mutex g_cache_mu;     // host-side bookkeeping only; GPU-side overlap still races
 
 // Table region layout (offsets in bytes from the table base, 256-aligned pieces).
 struct TableLayout {
@@ -145,21 +151,29 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return SEGSALSA_ERR_CUDA;
+  // the device address of the array in the current context (this also creates the context
+  // on first use), then the context's identity
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_static_scratch) != cudaSuccess || !sym) return SEGSALSA_ERR_CUDA;
+  const unsigned long long ctx = current_context_id();
+  std::lock_guard<std::mutex> lk(g_cache_mu);
   DevCache& dc = g_cache[dev];
-  if (!dc.base) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return SEGSALSA_ERR_CUDA;
-    dc.base = reinterpret_cast<unsigned char*>(p);
+  if (dc.base != sym || dc.ctx != ctx || ctx == 0) {
+    dc.base = reinterpret_cast<unsigned char*>(sym);
+    dc.ctx = ctx;
+    dc.H = dc.W = -1;  // tables unknown: rebuild
   }
   unsigned char* spec = dc.base;
   unsigned char* tb = dc.base + kSpecBytes;
   const TableLayout TL = table_layout(W, Mf, Wh);
+  bool rebuilt = false;
   if (dc.H != H || dc.W != W || dc.c != c_omega) {
     const int n = (Mf > W ? Mf : W);
     k_static_tables<<<(n + 255) / 256, 256, 0, st>>>(tb, H, W, Mf, Wh, blue, c_omega);
     k_static_bhat<<<(Mf + 127) / 128, 128, 0, st>>>(tb, W, Mf, Wh, blue);
     if (cudaGetLastError() != cudaSuccess) return SEGSALSA_ERR_CUDA;
     dc.H = H; dc.W = W; dc.c = c_omega;
+    rebuilt = true;
   }
 
   pl.tw = reinterpret_cast<const float2*>(tb + TL.tw);
@@ -191,7 +205,9 @@ extern "C" int segsalsa_str_linear_solve_static(const float* rhs, float* z, int3
   const int ncolblk = (Wh * K + CB - 1) / CB;
 
   const dim3 rg(nq, H);
-  if (launch_row<float>(true, ra, rg, rl, st) != cudaSuccess ||
+  // the forward row pass copies the tables before its programmatic-dependency wait, so right
+  // after a rebuild it must be an ordinary launch (it then starts once k_static_bhat is done)
+  if (launch_row<float>(true, ra, rg, rl, st, !rebuilt) != cudaSuccess ||
       launch_col<float>(ca, ncolblk, col_threads, col_smem, st) != cudaSuccess ||
       launch_row<float>(false, ra, rg, rl, st) != cudaSuccess)
     return SEGSALSA_ERR_CUDA;

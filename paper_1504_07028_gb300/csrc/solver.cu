@@ -69,6 +69,7 @@ struct SolverBase {
   virtual int clear_err(cudaStream_t s) = 0;
   virtual void invalidate() = 0;                       // forget p and the iterates
   virtual int set_g4(int mode) = 0;
+  virtual int set_wait_budget(long long cycles, int probe) = 0;
   virtual int set_log_probs(const void* logp, int layout, int dev) = 0;
   virtual int set_lambda(double lam) = 0;
   virtual int set_weights(const double* w) = 0;
@@ -410,6 +411,8 @@ class Solver : public SolverBase {
   bool use_graphs = true;
   int g4 = SEGSALSA_G4_AFFINE;   // MPO of g4: affine set (eq. 10) or probability simplex
   int gen = 0;
+  long long wait_budget = WAIT_BUDGET_CYCLES;  // bounded device-side waits (clock cycles)
+  int wait_probe = 0;            // 1: the next bulk-copy waits cannot complete (wait test)
 
   ~Solver() override {
     if (st) cudaStreamSynchronize(st);
@@ -600,6 +603,8 @@ class Solver : public SolverBase {
     a.diag_sq = b.dsq; a.omega = b.omega;
     a.tau = (T)(lambda / mu); a.mu = (T)mu; a.invK = (T)(1.0 / pl.K); a.sp = sp;
     a.err = b.err;
+    a.budget = wait_budget;
+    a.probe = wait_probe ? 16u : 0u;
     const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
     SGS_CUDA(launch(KIND_SWEEP, [&]() {
       if (g4 == SEGSALSA_G4_SIMPLEX) return launch_sweep_simplex<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
@@ -702,6 +707,8 @@ class Solver : public SolverBase {
     MlrArgs a{};
     a.x = xd; a.w = wd; a.bias = bd; a.p = b.tmp; a.err = b.err;
     a.n = pl.n; a.d = d; a.dpad = (d + 15) / 16 * 16; a.K = pl.K; a.npad = pl.K <= 16 ? 16 : 32;
+    a.budget = wait_budget;
+    a.probe = wait_probe ? 16u : 0u;
     SGS_CUDA(launch(KIND_MLR, [&]() { return launch_mlr<T>(a, st); }));
     int errflag = 0;
     SGS_CUDA(cudaMemcpyAsync(&errflag, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1038,6 +1045,16 @@ class Solver : public SolverBase {
   }
   void invalidate() override { have_probs = false; iter = 0; rhs_dense = false; }
   int generation() const override { return gen; }
+  int set_wait_budget(long long cycles, int probe) override {
+    if (cycles < 1) return fail(SEGSALSA_ERR_ARG, "the wait budget must be at least one cycle");
+    if (probe != 0 && probe != 1) return fail(SEGSALSA_ERR_ARG, "probe must be 0 or 1");
+    SGS_CUDA(cudaStreamSynchronize(st));
+    drop_chunks();                 // the graphs hold the old kernel arguments
+    wait_budget = cycles;
+    wait_probe = probe;
+    return SEGSALSA_OK;
+  }
+
   int set_g4(int mode) override {
     if (mode != SEGSALSA_G4_AFFINE && mode != SEGSALSA_G4_SIMPLEX) return fail(SEGSALSA_ERR_ARG, "bad g4 mode");
     if (mode == g4) return SEGSALSA_OK;
@@ -1830,6 +1847,9 @@ int segsalsa_str_set_spectra(segsalsa_str_t* h, const void* x, const void* w, co
 }
 int segsalsa_str_get_probs(segsalsa_str_t* h, void* p, int32_t layout, int32_t dev) {
   SGS_H(h); return h->impl->get_probs(p, layout, dev);
+}
+int segsalsa_str_set_wait_budget(segsalsa_str_t* h, int64_t cycles, int32_t probe) {
+  SGS_H(h); return h->impl->set_wait_budget((long long)cycles, probe);
 }
 int segsalsa_str_set_g4(segsalsa_str_t* h, int32_t mode) {
   SGS_H(h); return h->impl->set_g4(mode);

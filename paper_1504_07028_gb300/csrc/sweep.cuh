@@ -45,6 +45,8 @@ struct SweepArgs {
   T invK;
   int sp;                // 1, 2, 0 = infinity
   int* err;              // set to 1 when a bounded wait gives up
+  long long budget;      // clock cycles a bounded wait may take
+  uint32_t probe;        // extra bytes armed on the first row's barrier (0; 16 in the wait test)
 };
 
 // Coefficients of u2 = V A for the prox of tau*||.||_{S_p} at V (R x 2) with Gram
@@ -125,7 +127,7 @@ __host__ __device__ inline void stage_sizes(int NC, int L, int K, size_t& d2b, s
 template <typename T>
 __device__ __forceinline__ void issue_row(const SweepArgs<T>& a, size_t pix0, int TW, int L,
                                           unsigned char* st, size_t d2b, size_t dlb,
-                                          uint64_t* bar) {
+                                          uint64_t* bar, uint32_t extra = 0) {
   const int K = a.K;
   const char* g0 = reinterpret_cast<const char*>(a.d2) + pix0 * (2 * L * K * sizeof(T));
   const char* g1 = reinterpret_cast<const char*>(a.dloc) + pix0 * (3 * K * sizeof(T));
@@ -139,7 +141,7 @@ __device__ __forceinline__ void issue_row(const SweepArgs<T>& a, size_t pix0, in
   const uint32_t b0 = (uint32_t)al16((g0 - a0) + n0);
   const uint32_t b1 = (uint32_t)al16((g1 - a1) + n1);
   const uint32_t b2 = (uint32_t)al16((g2 - a2) + n2);
-  mbar_arrive_expect_tx(bar, b0 + b1 + b2);
+  mbar_arrive_expect_tx(bar, b0 + b1 + b2 + extra);
   bulk_g2s(st, a0, b0, bar);
   bulk_g2s(st + d2b, a1, b1, bar);
   bulk_g2s(st + d2b + dlb, a2, b2, bar);
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
   pdl_wait();  // z, d, p and the partial buffers belong to the previous kernels
   __syncthreads();
   if (threadIdx.x == 0) {
-    issue_row<T>(a, (size_t)y0 * a.W + x0, TW, L, stage0, d2b, dlb, &mbar[0]);
+    issue_row<T>(a, (size_t)y0 * a.W + x0, TW, L, stage0, d2b, dlb, &mbar[0], a.probe);
     if (TH > 1) issue_row<T>(a, (size_t)(y0 + 1) * a.W + x0, TW, L, stage0 + stb, d2b, dlb, &mbar[1]);
   }
   // z tile (with halo, periodic) by per-thread async copies; padded classes read as zero
@@ -294,12 +296,12 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
 
   for (int r = 0; r < TH; ++r) {
     const int sidx = r & 1;
-    const bool ok = mbar_wait_bounded(&mbar[sidx], (uint32_t)((r >> 1) & 1), WAIT_BUDGET_CYCLES);
+    const bool ok = mbar_wait_bounded(&mbar[sidx], (uint32_t)((r >> 1) & 1), a.budget);
     if (__syncthreads_or(!ok)) {
       // a copy never completed: report, give the other stage a bounded chance, and leave
       if (threadIdx.x == 0) {
         atomicExch(a.err, 1);
-        if (r + 1 < TH) mbar_wait_bounded(&mbar[sidx ^ 1], (uint32_t)(((r + 1) >> 1) & 1), WAIT_BUDGET_CYCLES);
+        if (r + 1 < TH) mbar_wait_bounded(&mbar[sidx ^ 1], (uint32_t)(((r + 1) >> 1) & 1), a.budget);
       }
       return;
     }
@@ -468,19 +470,14 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
 // Largest dynamic shared memory granted so far to each sweep variant.
 template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 struct SweepGrant {
-  static size_t v;
+  static SmemGrants v;
 };
 template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
-size_t SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v = 0;
+SmemGrants SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v;
 
 template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>
 inline cudaError_t grant_sweep(size_t smem) {
-  size_t& g = SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v;
-  if (smem <= g) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_sweep<T, M, G, DIAG, SIMP, KEQ>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) g = smem;
-  return e;
+  return grant_smem(k_sweep<T, M, G, DIAG, SIMP, KEQ>, smem, SweepGrant<T, M, G, DIAG, SIMP, KEQ>::v);
 }
 
 template <typename T, int M, int G, bool DIAG, bool SIMP, bool KEQ>

@@ -263,21 +263,18 @@ int zfused_max_clusters(int CS, int threads, size_t smem);
 #ifdef SGS_FFT_INSTANTIATE
 template <typename T>
 struct ZfGrant {
-  static size_t g;
-  static bool wide;
+  static SmemGrants g;
 };
-template <typename T> size_t ZfGrant<T>::g = 0;
-template <typename T> bool ZfGrant<T>::wide = false;
+template <typename T> SmemGrants ZfGrant<T>::g;
 
 template <typename T>
 static cudaError_t zfused_attrs(int CS, size_t smem) {
   cudaError_t e = grant_smem(k_zfused<T>, smem, ZfGrant<T>::g);
   if (e != cudaSuccess) return e;
-  if (CS > 8 && !ZfGrant<T>::wide) {
-    e = cudaFuncSetAttribute(k_zfused<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    ZfGrant<T>::wide = true;
-  }
+  // clusters above the portable size of 8: set on every call (the attribute belongs to the
+  // current device's context, and the fused form is an opt-in path)
+  if (CS > 8)
+    return cudaFuncSetAttribute(k_zfused<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return cudaSuccess;
 }
 
