@@ -77,7 +77,7 @@ def test_static_zero_weights_is_a_scaling(B):
         torch.cuda.synchronize()
         z = out.cpu().numpy()
         zo = _oracle(rhs_np, np.zeros(9), 1)
-        assert np.abs(zo - rhs_np / 3.0).max() < 1e-12
+        assert np.abs(zo - rhs_np.astype(np.float64) / 3.0).max() < 1e-12
         assert np.abs(z - zo).max() <= ORACLE_TOL * np.abs(zo).max(), call
 
 
