@@ -286,7 +286,12 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
  *                 memory (2, 4, 8 or 16); 1 = three launches (row transforms, column solves,
  *                 inverse row transforms); 0 = the library's choice (three launches: the
  *                 fused form measured slower on every shape tried). A fused request that the
- *                 band or the device cannot hold runs three launches (get_tiling reports 1). */
+ *                 band or the device cannot hold runs three launches (get_tiling reports 1).
+ *   row_pipe    : form of the two row-transform passes: 1 = one CTA per (row, class block);
+ *                 2 = persistent CTAs (one wave) that walk the (row, class block) units and
+ *                 copy the next unit's input into shared memory asynchronously while the
+ *                 current unit is transformed; 0 = the library's choice. Both forms give
+ *                 the same results. */
 typedef struct {
   int32_t tile_rows;
   int32_t row_pairs;
@@ -294,6 +299,7 @@ typedef struct {
   int32_t row_threads;
   int32_t col_rows;
   int32_t zfuse;
+  int32_t row_pipe;
 } segsalsa_str_tiling;
 
 /* create / workspace_bytes with an explicit tiling (NULL = defaults, same as the plain calls).
@@ -331,8 +337,8 @@ int segsalsa_str_batch_solve(segsalsa_str_batch_t* b, int32_t iters);
 /* Project-written autotuner. Groups the images by class (see batch_create), and for each
  * class, largest total work first, times `trial_iters` >= 1 batch iterations for every
  * candidate tiling of that class while the other classes keep their current tiling, keeping
- * the fastest (candidates: tile_rows 4..32, then row_pairs, col_block, row_threads and
- * col_rows in turn). The lane count
+ * the fastest (candidates: tile_rows 4..32, then row_pairs, col_block, row_threads,
+ * col_rows and row_pipe in turn). The lane count
  * is tuned first the same way (4, 8, 16, 32, n_images). The choice is
  * stored per class in a process-wide cache (used by later batch_create calls with tiling ==
  * NULL) and written to chosen[i] (nullable, n_images entries). The images are rebuilt with

@@ -59,18 +59,20 @@ class Params(C.Structure):
 
 class Tiling(C.Structure):
     _fields_ = [("tile_rows", C.c_int32), ("row_pairs", C.c_int32), ("col_block", C.c_int32),
-                ("row_threads", C.c_int32), ("col_rows", C.c_int32), ("zfuse", C.c_int32)]
+                ("row_threads", C.c_int32), ("col_rows", C.c_int32), ("zfuse", C.c_int32),
+                ("row_pipe", C.c_int32)]
 
     def as_tuple(self):
         return (self.tile_rows, self.row_pairs, self.col_block, self.row_threads, self.col_rows,
-                self.zfuse)
+                self.zfuse, self.row_pipe)
 
 
 def make_tiling(tile_rows=0, row_pairs=0, col_block=0, row_threads=0, col_rows=0,
-                zfuse=0) -> Tiling:
+                zfuse=0, row_pipe=0) -> Tiling:
     t = Tiling()
     t.tile_rows, t.row_pairs, t.col_block = int(tile_rows), int(row_pairs), int(col_block)
     t.row_threads, t.col_rows, t.zfuse = int(row_threads), int(col_rows), int(zfuse)
+    t.row_pipe = int(row_pipe)
     return t
 
 

@@ -27,11 +27,21 @@ namespace sgs {
 
 constexpr int FFT_MAXST = 24;
 
-// Shared-memory slot of complex element i of a transform buffer: one pad slot after every 8
-// elements. The Stockham stages write with power-of-two strides (radix x sequences); without
-// the pad those writes fall on a few banks, with it they spread over all of them.
-__host__ __device__ __forceinline__ int px(int i) { return i + (i >> 3); }
-__host__ __device__ inline size_t padded_elems(size_t n) { return n + (n >> 3) + 1; }
+// Shared-memory slot of complex element i of a transform buffer: one pad slot after every
+// 128 bytes of elements (16 FP32 or 8 FP64 complex values). The first Stockham stage writes
+// with a power-of-two stride (radix x sequences); without the pad those writes fall on a few
+// banks, with it they spread over all of them. A pad per 128 bytes keeps every contiguous,
+// 128-byte-aligned run of a warp's accesses (the stage loads, the later stages' stores) inside
+// one set of 32 banks; a pad per 64 bytes (the first version) made all of those 2-way
+// conflicted (half of the shared-memory wavefronts of the row passes were conflicts).
+template <typename T>
+struct PadShift {
+  static constexpr int v = sizeof(T) == 4 ? 4 : 3;
+};
+template <typename T>
+__host__ __device__ __forceinline__ int px(int i) { return i + (i >> PadShift<T>::v); }
+template <typename T>
+__host__ __device__ inline size_t padded_elems(size_t n) { return n + (n >> PadShift<T>::v) + 1; }
 
 template <typename T>
 struct FftPlan {
@@ -163,7 +173,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ Xin, cplx<
     const int j = t - g * Ns;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = Xin[px((t + r * nb) * S + b)];
+    for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * nb) * S + b)];
     // twiddles w^r, w = tw[j * stride]: w and (for R > 5) w^4 from the table, the other
     // powers by at most two products
     {
@@ -190,7 +200,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ Xin, cplx<
     Dft<R, C>::run(v);
     const int base = (g * Ns * R + j) * S + b;
 #pragma unroll
-    for (int r = 0; r < R; ++r) Xout[px(base + r * Ns * S)] = v[r];
+    for (int r = 0; r < R; ++r) Xout[px<T>(base + r * Ns * S)] = v[r];
   }
 }
 
@@ -219,7 +229,7 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* __restrict__ Xin,
       const int jj = t - qdiv(t, mg_ns) * Ns;
       const int e = r * jj * s;
       if (e) {
-        const int q = px(n * S + b);
+        const int q = px<T>(n * S + b);
         Xin[q] = cmul(Xin[q], tw[e]);
       }
     }
@@ -231,13 +241,13 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* __restrict__ Xin,
     const int rest = qdiv(it, mgB), b = it - rest * B;   // sequences fastest: shared loads
     const int t = rest / hm, m = rest - t * hm;
     const int src = t * S + b;
-    const C y0 = Xin[px(src)];
+    const C y0 = Xin[px<T>(src)];
     const int step = m * nb;                               // < Mf
     int idx = 0;
     T ax = T(0), ay = T(0), bx = T(0), by = T(0);
     for (int r = 1; r < hm; ++r) {
-      const C yr = Xin[px(src + r * nb * S)];
-      const C yq = Xin[px(src + (R - r) * nb * S)];
+      const C yr = Xin[px<T>(src + r * nb * S)];
+      const C yq = Xin[px<T>(src + (R - r) * nb * S)];
       idx += step;
       idx -= (idx >= Mf) ? Mf : 0;
       const C w = tw[idx];
@@ -249,8 +259,8 @@ __device__ __forceinline__ void fft_direct_stage(cplx<T>* __restrict__ Xin,
     const int g = qdiv(t, mg_ns), jj = t - g * Ns;
     const int ob = g * Ns * R + jj;
     // i (bx + i by) = -by + i bx
-    Xout[px((ob + m * Ns) * S + b)] = mkc<T>(y0.x + ax - by, y0.y + ay + bx);
-    if (m > 0) Xout[px((ob + (R - m) * Ns) * S + b)] = mkc<T>(y0.x + ax + by, y0.y + ay - bx);
+    Xout[px<T>((ob + m * Ns) * S + b)] = mkc<T>(y0.x + ax - by, y0.y + ay + bx);
+    if (m > 0) Xout[px<T>((ob + (R - m) * Ns) * S + b)] = mkc<T>(y0.x + ax + by, y0.y + ay - bx);
   }
 }
 
@@ -326,12 +336,12 @@ __device__ cplx<T>* dft_rows(cplx<T>* X, cplx<T>* Y, int B, uint32_t mgB, const 
   // a_n = x_n conj(chirp_n), zero padded (each thread rewrites only its own elements)
   for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x) {
     const int n = qdiv(i, mgB);
-    X[px(i)] = (n < pl.N) ? cmulc(X[px(i)], tb.chirp[n]) : mkc<T>(T(0), T(0));
+    X[px<T>(i)] = (n < pl.N) ? cmulc(X[px<T>(i)], tb.chirp[n]) : mkc<T>(T(0), T(0));
   }
   __syncthreads();
   cplx<T>* A = fft_forward<T>(X, Y, B, mgB, pl, tb.tw);
   for (int i = threadIdx.x; i < pl.Mf * B; i += blockDim.x)
-    A[px(i)] = cconj(cmul(A[px(i)], tb.bhat[qdiv(i, mgB)]));
+    A[px<T>(i)] = cconj(cmul(A[px<T>(i)], tb.bhat[qdiv(i, mgB)]));
   __syncthreads();
   return fft_forward<T>(A, A == X ? Y : X, B, mgB, pl, tb.tw);  // = conj(cyclic convolution)
 }
@@ -340,7 +350,7 @@ __device__ cplx<T>* dft_rows(cplx<T>* X, cplx<T>* Y, int B, uint32_t mgB, const 
 template <typename T>
 __device__ __forceinline__ cplx<T> dft_out(const cplx<T>* R, int B, int k, int b,
                                            const FftPlan<T>& pl, const FftTables<T>& tb) {
-  const cplx<T> v = R[px(k * B + b)];
+  const cplx<T> v = R[px<T>(k * B + b)];
   if (!pl.blue) return v;
   return cconj(cmul(tb.chirp[k], v));  // conj(chirp_k) * (a * b)_k
 }
@@ -363,6 +373,9 @@ struct RowArgs {
   const int* offX;       // [W][2]: (tile col * EHmax * EWmax + ext col) * K, -1 when absent
   cplx<T>* S;            // [H][Wh][K]
   T* z;                  // pass C output [n][K]
+  // persistent pipelined row passes (k_row_*_pipe): units (row, class block) in row-major
+  // order, nq class blocks per row, and the vertical-cover slots of the forward stage (1 or 2)
+  int nq, units, nslot;
 };
 
 // rhs(y, x, k) as the fixed-order sum of the (at most 2 x 2) tile partials covering (y, x);
@@ -466,7 +479,7 @@ __device__ __forceinline__ uint32_t div_magic_dev(int d) {
 // transform tables and of the horizontal offset table of the tile partials.
 template <typename T>
 __host__ __device__ inline size_t row_smem_bytes(int N, int Mf, int blue, int QB, int tables) {
-  return sizeof(cplx<T>) * 2 * padded_elems((size_t)Mf * QB) +
+  return sizeof(cplx<T>) * 2 * padded_elems<T>((size_t)Mf * QB) +
          (tables ? fft_table_bytes<T>(N, Mf, blue) + sizeof(int) * 2 * (size_t)N : 0);
 }
 template <typename T>
@@ -507,8 +520,8 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
-  C* Y = X + padded_elems((size_t)a.pl.Mf * B);  // second transform buffer
-  C* tab = Y + padded_elems((size_t)a.pl.Mf * B);
+  C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);  // second transform buffer
+  C* tab = Y + padded_elems<T>((size_t)a.pl.Mf * B);
   // horizontal offsets of the partials: a shared-memory copy, or the global table (cached
   // loads) when the CTA's shared memory is kept to the transform buffers
   const int* cX = a.offX;
@@ -554,11 +567,10 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
         const int i = i0 + u * blockDim.x;
         if (i < totv) {
           const int x = i >> lnv, j = i & (nv - 1);
+          // classes 2p, 2p + 1 of the vector form pair p (real, imaginary part)
 #pragma unroll
-          for (int e = 0; e < VE; ++e) {
-            const int c = j * VE + e;  // class within the CTA: pair c / 2, part c % 2
-            Xf[2 * px(x * B + (c >> 1)) + (c & 1)] = v16_at(v[u], e);
-          }
+          for (int pp = 0; pp < VE / 2; ++pp)
+            X[px<T>(x * B + j * (VE / 2) + pp)] = mkc<T>(v16_at(v[u], 2 * pp), v16_at(v[u], 2 * pp + 1));
         }
       }
     }
@@ -581,7 +593,7 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * blockDim.x;
-      if (i < tot) Xf[2 * px(i >> 1) + (i & 1)] = v[u];
+      if (i < tot) Xf[2 * px<T>(i >> 1) + (i & 1)] = v[u];
     }
   }
   __syncthreads();
@@ -632,8 +644,8 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
-  C* Y = X + padded_elems((size_t)a.pl.Mf * B);  // second transform buffer
-  C* tab = Y + padded_elems((size_t)a.pl.Mf * B);
+  C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);  // second transform buffer
+  C* tab = Y + padded_elems<T>((size_t)a.pl.Mf * B);
   const FftTables<T> tb = row_tables<T>(a, tab);
   cp_async_commit();
   pdl_wait();  // the spectrum comes from the column pass
@@ -668,7 +680,7 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
         C A = Av[u], Bq = Bv[u];
         if ((i >> a.lgB) >= a.Wh) { A = cconj(A); Bq = cconj(Bq); }
         C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);   // conj(A + i B)
-        X[px(i)] = xv;
+        X[px<T>(i)] = xv;
       }
     }
   }
@@ -710,6 +722,288 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
     const C v = dft_out<T>(R, B, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
     a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
   }
+}
+
+// ------------------------------------------------ pipelined row passes (persistent CTAs)
+//
+// The same transforms as k_row_forward / k_row_inverse, organised for long rows: a CTA stays
+// resident and walks the units (row y, class block) u = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Each unit's input (the tile partials that cover row y, the dense rhs row, or the spectrum
+// row) is brought into a shared-memory stage by asynchronous copies; the copies of the next
+// unit are issued as soon as the current unit has left the stage, so they are in flight while
+// the current unit's FFT and stores run. Every CTA thus keeps loads outstanding during its
+// compute phases, instead of alternating between loading and computing. The summation order
+// of the covers and the transforms are those of the one-unit-per-CTA kernels (bit-identical
+// results).
+
+// 16-byte asynchronous copy global -> shared that bypasses L1 (streamed data).
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+
+// Shared memory of a pipelined row CTA: two transform buffers, then the stage.
+template <typename T>
+__host__ __device__ inline size_t rowpipe_fwd_stage_elems(int N, int ntx, int EWmax, int QB,
+                                                          bool dense) {
+  return dense ? (size_t)N * 2 * QB : (size_t)ntx * EWmax * 2 * QB;  // per slot, in T
+}
+template <typename T>
+__host__ __device__ inline size_t rowpipe_smem_bytes(bool forward, int N, int Mf, int Wh, int QB,
+                                                     int ntx, int EWmax, int nslot, bool dense) {
+  const size_t xy = sizeof(cplx<T>) * 2 * padded_elems<T>((size_t)Mf * QB);
+  if (forward)
+    return xy + sizeof(T) * (dense ? 1 : nslot) *
+                    rowpipe_fwd_stage_elems<T>(N, ntx, EWmax, QB, dense);
+  return xy + sizeof(cplx<T>) * (size_t)Wh * 2 * QB;
+}
+
+// Issue the copies of the rhs of unit u into the stage: vertical covers [iy0, iy1) of row y
+// (slot iy - iy0 each, laid out [tile column][ext column][class of the block]), or the dense
+// rhs row ([x][class]). Classes past K are zero-filled.
+template <typename T>
+__device__ __forceinline__ void rowpipe_issue_fwd(const RowArgs<T>& a, int u, int iy0, int iy1,
+                                                  T* stg, size_t slot) {
+  const int y = u / a.nq, qb = u - y * a.nq;
+  const int CW = 2 * a.QB;             // classes of the unit
+  const int c0 = qb * CW;
+  const int K = a.K;
+  constexpr int VE = 16 / sizeof(T);
+  const bool vec = CW % VE == 0 && K % VE == 0 && c0 + CW <= K;
+  const int nv = CW / VE;
+  if (a.src) {
+    const T* row = a.src + (size_t)y * a.W * K + c0;
+    if (vec && (reinterpret_cast<uintptr_t>(a.src) & 15) == 0) {
+      for (int i = threadIdx.x; i < a.W * nv; i += blockDim.x) {
+        const int x = i / nv, v = i - x * nv;
+        cp_async_cg16(stg + (size_t)x * CW + v * VE, row + (size_t)x * K + v * VE);
+      }
+    } else {
+      for (int i = threadIdx.x; i < a.W * CW; i += blockDim.x) {
+        const int x = i / CW, c = i - x * CW;
+        const bool ok = c0 + c < K;
+        cp_async_zfill<sizeof(T)>(stg + i, ok ? row + (size_t)x * K + c : a.src, ok);
+      }
+    }
+    return;
+  }
+  const size_t tstride = (size_t)a.EHmax * a.EWmax * K;  // P elements per tile
+  const int R = a.ntx * a.EWmax;                          // stage rows per slot
+  for (int iy = iy0; iy < iy1; ++iy) {
+    const int cy = a.covY[2 * y + iy];
+    if (cy < 0) continue;                                 // uniform over the CTA
+    const T* base = a.P + cover_row_base(a, cy) + c0;
+    T* dst = stg + (size_t)(iy - iy0) * slot;
+    if (vec) {
+      for (int i = threadIdx.x; i < R * nv; i += blockDim.x) {
+        const int r = i / nv, v = i - r * nv;
+        const int tx = r / a.EWmax, ex = r - tx * a.EWmax;
+        cp_async_cg16(dst + (size_t)r * CW + v * VE, base + tx * tstride + (size_t)ex * K + v * VE);
+      }
+    } else {
+      for (int i = threadIdx.x; i < R * CW; i += blockDim.x) {
+        const int r = i / CW, c = i - r * CW;
+        const int tx = r / a.EWmax, ex = r - tx * a.EWmax;
+        const bool ok = c0 + c < K;
+        cp_async_zfill<sizeof(T)>(dst + i, ok ? base + tx * tstride + (size_t)ex * K + c : a.P, ok);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_forward_pipe(const RowArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int B = a.QB, N = a.pl.N;
+  const int CW = 2 * B;
+  C* X = reinterpret_cast<C*>(smem_raw);
+  C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);
+  T* stg = reinterpret_cast<T*>(Y + padded_elems<T>((size_t)a.pl.Mf * B));
+  const bool dense = a.src != nullptr;
+  const size_t slot = rowpipe_fwd_stage_elems<T>(N, a.ntx, a.EWmax, B, dense);
+  const FftTables<T> tb{a.pl.tw, a.pl.chirp, a.pl.bhat};
+  pdl_wait();                              // the partials / rhs come from the previous kernel
+  int u = blockIdx.x;
+  if (u < a.units) rowpipe_issue_fwd<T>(a, u, 0, dense ? 1 : a.nslot, stg, slot);
+  cp_async_commit();
+  for (; u < a.units; u += gridDim.x) {
+    const int y = u / a.nq, qb = u - y * a.nq;
+    const int q0 = qb * B;
+    const bool hy = !dense && a.covY[2 * y + 1] >= 0;
+    cp_async_wait_all();
+    __syncthreads();                       // stage of u landed; the previous unit is done
+    // the stage holds classes (2q, 2q + 1) of a pixel next to each other: read them as the
+    // complex value of pair q
+    const C* sc = reinterpret_cast<const C*>(stg);
+    const C zero = mkc<T>(T(0), T(0));
+    if (dense) {
+      for (int i = threadIdx.x; i < N * B; i += blockDim.x) X[px<T>(i)] = sc[i];
+    } else {
+      // v = p00 (+ p01) (+ p10) (+ p11): the order of gather_row; absent covers add +0
+      const C* s1 = sc + slot / 2;
+      const bool two = a.nslot == 2;
+      for (int i = threadIdx.x; i < N * B; i += blockDim.x) {
+        const int x = i >> a.lgB, q = i & (B - 1);
+        const int2 cx = __ldg(reinterpret_cast<const int2*>(a.covX) + x);
+        const int r0 = (cx.x >> 16) * a.EWmax + (cx.x & 0xffff);
+        const bool hx = cx.y >= 0;
+        const int r1 = hx ? (cx.y >> 16) * a.EWmax + (cx.y & 0xffff) : r0;
+        C v = sc[r0 * B + q];
+        v = cadd(v, hx ? sc[r1 * B + q] : zero);
+        if (two) {
+          v = cadd(v, hy ? s1[r0 * B + q] : zero);
+          v = cadd(v, (hx && hy) ? s1[r1 * B + q] : zero);
+        } else if (!hy) {
+          v = cadd(v, zero);
+          v = cadd(v, zero);
+        }
+        X[px<T>(i)] = v;
+      }
+      if (!two && hy) {
+        // one slot: the second vertical cover goes through the stage after the first
+        __syncthreads();
+        rowpipe_issue_fwd<T>(a, u, 1, 2, stg, slot);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        for (int i = threadIdx.x; i < N * B; i += blockDim.x) {
+          const int x = i >> a.lgB, q = i & (B - 1);
+          const int2 cx = __ldg(reinterpret_cast<const int2*>(a.covX) + x);
+          const int r0 = (cx.x >> 16) * a.EWmax + (cx.x & 0xffff);
+          const bool hx = cx.y >= 0;
+          const int r1 = hx ? (cx.y >> 16) * a.EWmax + (cx.y & 0xffff) : r0;
+          C v = X[px<T>(i)];
+          v = cadd(v, sc[r0 * B + q]);
+          v = cadd(v, hx ? sc[r1 * B + q] : zero);
+          X[px<T>(i)] = v;
+        }
+      }
+    }
+    __syncthreads();                       // the stage is free, X holds the unit's rows
+    const int un = u + gridDim.x;
+    if (un < a.units) rowpipe_issue_fwd<T>(a, un, 0, dense ? 1 : a.nslot, stg, slot);
+    cp_async_commit();
+    if (un >= a.units) pdl_trigger();
+    const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
+    // unpack the two real spectra of each pair (as k_row_forward)
+    for (int i = threadIdx.x; i < a.Wh * B; i += blockDim.x) {
+      const int qq = i & (B - 1);
+      const int kx = i >> a.lgB;
+      const int k = 2 * (q0 + qq);
+      if (k >= a.K) continue;
+      const C uu = dft_out<T>(R, B, kx, qq, a.pl, tb);
+      const C w = dft_out<T>(R, B, (kx == 0) ? 0 : N - kx, qq, a.pl, tb);
+      C oa, ob;
+      oa.x = T(0.5) * (uu.x + w.x); oa.y = T(0.5) * (uu.y - w.y);
+      ob.x = T(0.5) * (uu.y + w.y); ob.y = T(0.5) * (w.x - uu.x);
+      C* dst = a.S + ((size_t)y * a.Wh + kx) * a.K + k;
+      if ((a.K & 1) == 0) {
+        store_pair(dst, oa, ob);
+      } else {
+        dst[0] = oa;
+        if (k + 1 < a.K) dst[1] = ob;
+      }
+    }
+  }
+  cp_async_wait_all();                     // nothing may be in flight when the CTA exits
+}
+
+// Issue the copies of the spectrum row of unit u: [kx][class of the block] complex, kx < Wh.
+template <typename T>
+__device__ __forceinline__ void rowpipe_issue_inv(const RowArgs<T>& a, int u, cplx<T>* stg) {
+  using C = cplx<T>;
+  const int y = u / a.nq, qb = u - y * a.nq;
+  const int CW = 2 * a.QB;
+  const int c0 = qb * CW;
+  const C* row = a.S + (size_t)y * a.Wh * a.K + c0;
+  constexpr int PE = 16 / sizeof(C);       // complex values per 16 bytes (2 FP32, 1 FP64)
+  const bool vec = a.K % PE == 0 && c0 + CW <= a.K;
+  if (vec) {
+    const int nv = CW / PE;
+    for (int i = threadIdx.x; i < a.Wh * nv; i += blockDim.x) {
+      const int kx = i / nv, v = i - kx * nv;
+      cp_async_cg16(stg + (size_t)kx * CW + v * PE, row + (size_t)kx * a.K + v * PE);
+    }
+  } else {
+    for (int i = threadIdx.x; i < a.Wh * CW; i += blockDim.x) {
+      const int kx = i / CW, c = i - kx * CW;
+      const bool ok = c0 + c < a.K;
+      cp_async_zfill<sizeof(C)>(stg + i, ok ? row + (size_t)kx * a.K + c : a.S, ok);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_inverse_pipe(const RowArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int B = a.QB, N = a.pl.N;
+  const int CW = 2 * B;
+  C* X = reinterpret_cast<C*>(smem_raw);
+  C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);
+  C* stg = Y + padded_elems<T>((size_t)a.pl.Mf * B);
+  const FftTables<T> tb{a.pl.tw, a.pl.chirp, a.pl.bhat};
+  pdl_wait();                              // the spectrum comes from the column pass
+  int u = blockIdx.x;
+  if (u < a.units) rowpipe_issue_inv<T>(a, u, stg);
+  cp_async_commit();
+  const T inv = T(1) / T(N);
+  constexpr int VE = 16 / sizeof(T);
+  for (; u < a.units; u += gridDim.x) {
+    const int y = u / a.nq, qb = u - y * a.nq;
+    const int q0 = qb * B;
+    cp_async_wait_all();
+    __syncthreads();
+    // conj(A + iB) over the full frequency range (Hermitian extension), as k_row_inverse
+    for (int i = threadIdx.x; i < N * B; i += blockDim.x) {
+      const int qq = i & (B - 1);
+      const int kx = i >> a.lgB;
+      const int ks = kx < a.Wh ? kx : N - kx;
+      C A = stg[(size_t)ks * CW + 2 * qq], Bq = stg[(size_t)ks * CW + 2 * qq + 1];
+      if (kx >= a.Wh) { A = cconj(A); Bq = cconj(Bq); }
+      C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);
+      X[px<T>(i)] = xv;
+    }
+    __syncthreads();
+    const int un = u + gridDim.x;
+    if (un < a.units) rowpipe_issue_inv<T>(a, un, stg);
+    cp_async_commit();
+    if (un >= a.units) pdl_trigger();
+    const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
+    const bool vec = a.K % VE == 0 && (2 * B) % VE == 0 && 2 * (q0 + B) <= a.K &&
+                     (reinterpret_cast<uintptr_t>(a.z) & 15) == 0;
+    if (vec) {
+      const int nv = 2 * B / VE;
+      const int lnv = __ffs(nv) - 1;
+      for (int i = threadIdx.x; i < N * nv; i += blockDim.x) {
+        const int x = i >> lnv, j = i & (nv - 1);
+        T o[VE];
+#pragma unroll
+        for (int e = 0; e < VE / 2; ++e) {
+          const C v = dft_out<T>(R, B, x, j * (VE / 2) + e, a.pl, tb);
+          o[2 * e] = v.x * inv;
+          o[2 * e + 1] = -v.y * inv;
+        }
+        T* dst = a.z + ((size_t)y * a.W + x) * a.K + 2 * q0 + j * VE;
+        if constexpr (sizeof(T) == 4)
+          *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        else
+          *reinterpret_cast<double2*>(dst) = make_double2(o[0], o[1]);
+      }
+    } else {
+      for (int i = threadIdx.x; i < N * B * 2; i += blockDim.x) {
+        const int part = i & 1;
+        const int qq = (i >> 1) & (B - 1);
+        const int x = (i >> 1) >> a.lgB;
+        const int k = 2 * (q0 + qq) + part;
+        if (k >= a.K) continue;
+        const C v = dft_out<T>(R, B, x, qq, a.pl, tb);
+        a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
+      }
+    }
+  }
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ pass B (column solve)
@@ -956,6 +1250,14 @@ cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem
 // Grant the dynamic shared memory of the row / column kernels of a plan before any launch.
 template <typename T>
 cudaError_t prepare_fft(const RowLaunch& rl, size_t col_smem);
+// Pipelined row passes: launch on `grid` persistent CTAs of 256 threads, and the number of
+// such CTAs one SM holds with `smem` bytes of dynamic shared memory (after granting it).
+constexpr int ROWPIPE_THREADS = 256;
+template <typename T>
+cudaError_t launch_row_pipe(bool forward, const RowArgs<T>& a, int grid, size_t smem,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks);
 
 
 #ifdef SGS_FFT_INSTANTIATE
@@ -1000,6 +1302,39 @@ cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLa
 }
 
 template <typename T>
+struct RowPipeGrant {
+  static SmemGrants f, i;
+};
+template <typename T> SmemGrants RowPipeGrant<T>::f;
+template <typename T> SmemGrants RowPipeGrant<T>::i;
+
+template <typename T>
+cudaError_t launch_row_pipe(bool forward, const RowArgs<T>& a, int grid, size_t smem,
+                            cudaStream_t st) {
+  cudaError_t e;
+  if (forward) {
+    if ((e = grant_smem(k_row_forward_pipe<T>, smem, RowPipeGrant<T>::f)) != cudaSuccess) return e;
+    return launch_pdl(k_row_forward_pipe<T>, dim3(grid), dim3(ROWPIPE_THREADS), smem, st, a);
+  }
+  if ((e = grant_smem(k_row_inverse_pipe<T>, smem, RowPipeGrant<T>::i)) != cudaSuccess) return e;
+  return launch_pdl(k_row_inverse_pipe<T>, dim3(grid), dim3(ROWPIPE_THREADS), smem, st, a);
+}
+
+template <typename T>
+cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks) {
+  cudaError_t e;
+  *blocks = 0;
+  if (forward) {
+    if ((e = grant_smem(k_row_forward_pipe<T>, smem, RowPipeGrant<T>::f)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_forward_pipe<T>,
+                                                         ROWPIPE_THREADS, smem);
+  }
+  if ((e = grant_smem(k_row_inverse_pipe<T>, smem, RowPipeGrant<T>::i)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_inverse_pipe<T>,
+                                                       ROWPIPE_THREADS, smem);
+}
+
+template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem,
                               cudaStream_t st) {
   cudaError_t e = grant_smem(k_col_solve<T>, smem, ColGrant<T>::g);
@@ -1014,6 +1349,10 @@ extern template cudaError_t launch_col<float>(const ColArgs<float>&, int, int, s
 extern template cudaError_t launch_col<double>(const ColArgs<double>&, int, int, size_t, cudaStream_t);
 extern template cudaError_t prepare_fft<float>(const RowLaunch&, size_t);
 extern template cudaError_t prepare_fft<double>(const RowLaunch&, size_t);
+extern template cudaError_t launch_row_pipe<float>(bool, const RowArgs<float>&, int, size_t, cudaStream_t);
+extern template cudaError_t launch_row_pipe<double>(bool, const RowArgs<double>&, int, size_t, cudaStream_t);
+extern template cudaError_t row_pipe_blocks_per_sm<float>(bool, size_t, int*);
+extern template cudaError_t row_pipe_blocks_per_sm<double>(bool, size_t, int*);
 
 #endif
 

@@ -35,6 +35,8 @@ enum Kind { KIND_SWEEP = 0, KIND_ROWF = 1, KIND_COL = 2, KIND_ROWI = 3, KIND_DIA
 constexpr int NKIND = 9;
 constexpr int MAXCOV = 2;           // tile covers per row / column in the partial gather
 constexpr int TRACE_CAP = 128;      // device trace records before a flush to the host
+// Images from this many pixels up run the pipelined row passes unless the tiling says otherwise.
+constexpr long long ROWPIPE_DEFAULT_PIXELS = 1LL << 62;
 
 static thread_local std::string g_last_error;
 
@@ -132,6 +134,11 @@ struct Plan {
   size_t sweep_smem, sweep_smem_diag;
   int Wh, Mf, blue, QB, nqblk;
   RowLaunch row;
+  // pipelined row passes (persistent CTAs): on/off, vertical-cover stage slots, shared memory
+  // of the forward (enough for the partial and the dense source) and inverse kernels, grids
+  int rp, rp_nslot;
+  size_t rp_smem_f, rp_smem_i;
+  int rp_grid_f, rp_grid_i;
   int CB, NSEG, SL, col_threads, ncolblk;
   int row_threads, col_rows;   // target threads of a row-pass CTA; rows per column segment
   size_t col_smem;
@@ -168,6 +175,7 @@ static int check_tiling(const segsalsa_str_tiling* t, std::string& msg) {
   if (t->zfuse && t->zfuse != 1 && t->zfuse != 2 && t->zfuse != 4 && t->zfuse != 8 && t->zfuse != 16) {
     msg = "zfuse must be 0, 1, 2, 4, 8 or 16"; return SEGSALSA_ERR_ARG;
   }
+  if (t->row_pipe < 0 || t->row_pipe > 2) { msg = "row_pipe must be 0, 1 or 2"; return SEGSALSA_ERR_ARG; }
   return SEGSALSA_OK;
 }
 
@@ -249,6 +257,21 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   if (tl && tl->row_threads) pl.row_threads = floor_pow2(tl->row_threads);
   pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB, pl.row_threads);
   if (pl.row.smem > 227 * 1024) { msg = "row too long for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
+  // pipelined row passes: on request (row_pipe = 2) or by default (row_pipe = 0) for images
+  // of ROWPIPE_DEFAULT_PIXELS and more; the stage takes both vertical covers of a row at once
+  // while two CTAs still share an SM
+  {
+    const int req = tl ? tl->row_pipe : 0;
+    pl.rp = (req == 2 || (req == 0 && (long long)H * W >= ROWPIPE_DEFAULT_PIXELS)) ? 1 : 0;
+    const size_t two = rowpipe_smem_bytes<T>(true, W, pl.Mf, pl.Wh, pl.QB, pl.ntx, pl.EWmax, 2, false);
+    pl.rp_nslot = two <= 112 * 1024 ? 2 : 1;
+    pl.rp_smem_f = std::max(
+        rowpipe_smem_bytes<T>(true, W, pl.Mf, pl.Wh, pl.QB, pl.ntx, pl.EWmax, pl.rp_nslot, false),
+        rowpipe_smem_bytes<T>(true, W, pl.Mf, pl.Wh, pl.QB, pl.ntx, pl.EWmax, 1, true));
+    pl.rp_smem_i = rowpipe_smem_bytes<T>(false, W, pl.Mf, pl.Wh, pl.QB, pl.ntx, pl.EWmax, 1, false);
+    if (std::max(pl.rp_smem_f, pl.rp_smem_i) > 227 * 1024) pl.rp = 0;
+    pl.rp_grid_f = pl.rp_grid_i = 0;  // set at create (occupancy of the device)
+  }
   // column solve: column blocks of CB complex values, all H rows in shared memory (<= 64 KiB
   // so that several CTAs share an SM), NSEG segments per column
   pl.CB = sizeof(T) == 4 ? 8 : 4;
@@ -454,6 +477,18 @@ class Solver : public SolverBase {
     else SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
     if (pl.zf_cs && zfused_max_clusters<T>(pl.zf_cs, pl.zf_threads, pl.zf_smem) < 1) pl.zf_cs = 0;
+    if (pl.rp) {
+      // one wave of persistent CTAs; three launches of the one-unit kernels if none fits
+      int dev = 0, nsm = 0, nbf = 0, nbi = 0;
+      SGS_CUDA(cudaGetDevice(&dev));
+      SGS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      SGS_CUDA(row_pipe_blocks_per_sm<T>(true, pl.rp_smem_f, &nbf));
+      SGS_CUDA(row_pipe_blocks_per_sm<T>(false, pl.rp_smem_i, &nbi));
+      const long long units = (long long)pl.nqblk * pl.H;
+      pl.rp_grid_f = (int)std::min<long long>(units, (long long)nbf * nsm);
+      pl.rp_grid_i = (int)std::min<long long>(units, (long long)nbi * nsm);
+      if (nbf < 1 || nbi < 1) pl.rp = 0;
+    }
     return upload_tables();
   }
 
@@ -569,6 +604,7 @@ class Solver : public SolverBase {
     a.pl = fft_plan();
     a.src = src; a.P = b.P; a.ntx = pl.ntx; a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
     a.covY = b.covY; a.covX = b.covX; a.offX = b.offX; a.S = b.S; a.z = zout;
+    a.nq = pl.nqblk; a.units = pl.nqblk * pl.H; a.nslot = pl.rp_nslot;
     return a;
   }
 
@@ -586,12 +622,18 @@ class Solver : public SolverBase {
       return SEGSALSA_OK;
     }
     const dim3 rg(pl.nqblk, pl.H);
-    SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
+    if (pl.rp)
+      SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row_pipe<T>(true, ra, pl.rp_grid_f, pl.rp_smem_f, st); }));
+    else
+      SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
     ColArgs<T> ca{};
     ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG; ca.SL = pl.SL;
     ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
     SGS_CUDA(launch(KIND_COL, [&]() { return launch_col<T>(ca, pl.ncolblk, pl.col_threads, pl.col_smem, st); }));
-    SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row<T>(false, ra, rg, pl.row, st); }));
+    if (pl.rp)
+      SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row_pipe<T>(false, ra, pl.rp_grid_i, pl.rp_smem_i, st); }));
+    else
+      SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row<T>(false, ra, rg, pl.row, st); }));
     return SEGSALSA_OK;
   }
 
@@ -997,6 +1039,7 @@ class Solver : public SolverBase {
     t.tile_rows = pl.THmax; t.row_pairs = pl.QB; t.col_block = pl.CB;
     t.row_threads = pl.row_threads; t.col_rows = pl.col_rows;
     t.zfuse = pl.zf_cs ? pl.zf_cs : 1;
+    t.row_pipe = pl.rp ? 2 : 1;
     return t;
   }
 
@@ -1337,7 +1380,8 @@ static TuneKey tune_key(const segsalsa_str_params& p) {
 }
 static bool same_tiling(const segsalsa_str_tiling& a, const segsalsa_str_tiling& b) {
   return a.tile_rows == b.tile_rows && a.row_pairs == b.row_pairs && a.col_block == b.col_block &&
-         a.row_threads == b.row_threads && a.col_rows == b.col_rows && a.zfuse == b.zfuse;
+         a.row_threads == b.row_threads && a.col_rows == b.col_rows && a.zfuse == b.zfuse &&
+         a.row_pipe == b.row_pipe;
 }
 
 constexpr int BATCH_CHUNK = 64;         // iterations per captured graph
@@ -1667,6 +1711,7 @@ struct segsalsa_str_batch {
     const int cand_cols[] = {1, 2, 4, 8};
     const int cand_rthr[] = {128, 256, 512, 1024};
     const int cand_seg[] = {8, 16, 32};
+    const int cand_pipe[] = {1, 2};
     for (auto& o : order) {
       const std::vector<int>& mem = groups[o.second];
       segsalsa_str_tiling cur = req[mem[0]];
@@ -1684,20 +1729,22 @@ struct segsalsa_str_batch {
           if (rc) return false;
           key.push_back(pl.THmax); key.push_back(pl.QB); key.push_back(pl.CB);
           key.push_back(pl.row.threads); key.push_back(pl.NSEG); key.push_back(pl.zf_cs);
+          key.push_back(pl.rp);
         }
         return true;
       };
       std::vector<int> key;
       if (resolved(cur, key)) seen.insert(key);
-      for (int f = 0; f < 5; ++f) {
-        const int* cvs[5] = {cand_rows, cand_pairs, cand_cols, cand_rthr, cand_seg};
-        const int ncs[5] = {7, 5, 4, 4, 3};
+      for (int f = 0; f < 6; ++f) {
+        const int* cvs[6] = {cand_rows, cand_pairs, cand_cols, cand_rthr, cand_seg, cand_pipe};
+        const int ncs[6] = {7, 5, 4, 4, 3, 2};
         const int* cv = cvs[f];
         const int nc = ncs[f];
         segsalsa_str_tiling keep = cur;
         for (int c = 0; c < nc; ++c) {
           segsalsa_str_tiling t = cur;
-          int* fld[5] = {&t.tile_rows, &t.row_pairs, &t.col_block, &t.row_threads, &t.col_rows};
+          int* fld[6] = {&t.tile_rows, &t.row_pairs, &t.col_block, &t.row_threads, &t.col_rows,
+                         &t.row_pipe};
           *fld[f] = cv[c];
           if (!resolved(t, key) || seen.count(key)) continue;
           seen.insert(key);

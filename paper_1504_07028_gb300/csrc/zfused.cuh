@@ -47,7 +47,7 @@ __host__ __device__ inline size_t zf_smem_bytes(int N, int Mf, int blue, int Wh,
                                                 int tables) {
   const size_t B = (size_t)RMAX * QG;
   const size_t nseq = (size_t)Wh * 4 * QG;
-  return sizeof(cplx<T>) * 2 * padded_elems((size_t)Mf * B) +
+  return sizeof(cplx<T>) * 2 * padded_elems<T>((size_t)Mf * B) +
          (tables ? fft_table_bytes<T>(N, Mf, blue) : 0) + sizeof(int) * 2 * (size_t)N +
          sizeof(int) * 2 * (size_t)RMAX + sizeof(T) * (RMAX + 1) * nseq;
 }
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(512) k_zfused(const ZfArgs<T> a) {
   const int B = a.RMAX * QG;                      // sequences: b = row * QG + pair
   const int nseq = Wh * 4 * QG;                   // real sequences: (kx, class, re/im)
   C* X = reinterpret_cast<C*>(smem_raw);
-  C* Y = X + padded_elems((size_t)Mf * B);
-  C* tab = Y + padded_elems((size_t)Mf * B);
+  C* Y = X + padded_elems<T>((size_t)Mf * B);
+  C* tab = Y + padded_elems<T>((size_t)Mf * B);
   int* cX = reinterpret_cast<int*>(
       tab + (ra.smem_tables ? fft_table_bytes<T>(N, Mf, ra.pl.blue) / sizeof(C) : 0));
   int* rbs = cX + 2 * N;                          // [RMAX][2] vertical cover bases
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(512) k_zfused(const ZfArgs<T> a) {
           const int qq = t % QG, rx = t / QG;
           const int rr = rx / N, x = rx - rr * N;
           const int k = 2 * (q0 + qq) + part;
-          dst[u] = 2 * px(x * B + rr * QG + qq) + part;
+          dst[u] = 2 * px<T>(x * B + rr * QG + qq) + part;
           if (k < K)
             v[u] = ra.src ? ra.src[((size_t)(y0 + rr) * W + x) * K + k]
                           : gather_row<T>(ra.P, rbs[2 * rr], rbs[2 * rr + 1], cX, x, k);
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(512) k_zfused(const ZfArgs<T> a) {
     for (int i = threadIdx.x; i < (a.RMAX - R) * N * QG; i += blockDim.x) {
       const int qq = i % QG, rx = i / QG;
       const int rr = R + rx / N, x = rx % N;
-      X[px(x * B + rr * QG + qq)] = mkc<T>(T(0), T(0));
+      X[px<T>(x * B + rr * QG + qq)] = mkc<T>(T(0), T(0));
     }
   }
   __syncthreads();
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(512) k_zfused(const ZfArgs<T> a) {
     C xv;
     xv.x = A.x - Bq.y;
     xv.y = -(A.y + Bq.x);  // conj(A + i B)
-    X[px(kx * B + rr * QG + qq)] = xv;
+    X[px<T>(kx * B + rr * QG + qq)] = xv;
   }
   __syncthreads();
   const C* Rb = dft_rows<T>(X, Y, B, a.mgB, ra.pl, tb);

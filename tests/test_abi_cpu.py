@@ -77,9 +77,9 @@ def test_weights_validation(lib):
 
 
 def test_tiling_struct_matches_header():
-    assert ctypes.sizeof(B.Tiling) == 24
+    assert ctypes.sizeof(B.Tiling) == 28
     assert B.Tiling.row_pairs.offset == 4 and B.Tiling.col_rows.offset == 16
-    assert B.Tiling.zfuse.offset == 20
+    assert B.Tiling.zfuse.offset == 20 and B.Tiling.row_pipe.offset == 24
 
 
 @pytest.mark.parametrize("tiling,ok", [
@@ -87,7 +87,9 @@ def test_tiling_struct_matches_header():
     ((33, 0, 0), False), ((8, -1, 0), False), ((8, 0, 9), False), ((8, 65, 0), False),
     ((0, 0, 0, 256, 16), True), ((0, 0, 0, 32, 0), False), ((0, 0, 0, 2048, 0), False),
     ((0, 0, 0, 0, 1), False), ((0, 0, 0, 0, 0, 1), True), ((0, 0, 0, 0, 0, 16), True),
-    ((0, 0, 0, 0, 0, 3), False), ((0, 0, 0, 0, 0, 32), False), ((0, 0, 0, 0, 0, -1), False)])
+    ((0, 0, 0, 0, 0, 3), False), ((0, 0, 0, 0, 0, 32), False), ((0, 0, 0, 0, 0, -1), False),
+    ((0, 0, 0, 0, 0, 0, 1), True), ((0, 0, 0, 0, 0, 0, 2), True), ((0, 0, 0, 0, 0, 0, 3), False),
+    ((0, 0, 0, 0, 0, 0, -1), False)])
 def test_tiling_checks(lib, tiling, ok):
     pr = B.make_params(145, 145, 16)
     t = B.make_tiling(*tiling)
