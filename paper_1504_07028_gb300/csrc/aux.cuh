@@ -69,12 +69,61 @@ __global__ void k_labels(const T* z, int n, int K, int32_t* lab) {
   lab[i] = arg;
 }
 
+// G consecutive values of a pixel's classes (K valid, the rest zero): 16-byte loads when the
+// row of K values is 16-byte aligned and a whole number of vectors, scalar loads otherwise.
+template <typename T, int G>
+__device__ __forceinline__ void load_classes(const T* __restrict__ src, int K, T (&v)[G]) {
+  constexpr int VE = 16 / sizeof(T);
+  if (K % VE == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+#pragma unroll
+    for (int k0 = 0; k0 < G; k0 += VE) {
+      if (k0 < K) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 w = __ldg(reinterpret_cast<const float4*>(src + k0));
+          v[k0] = w.x; v[k0 + 1] = w.y; v[k0 + 2] = w.z; v[k0 + 3] = w.w;
+        } else {
+          const double2 w = __ldg(reinterpret_cast<const double2*>(src + k0));
+          v[k0] = w.x; v[k0 + 1] = w.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) v[k0 + e] = T(0);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < G; ++k) v[k] = k < K ? __ldg(src + k) : T(0);
+  }
+}
+
+// The 16 / sizeof(T) classes k0, k0 + 1, ... of a pixel's row of K values (zero past K): one
+// 16-byte load when they are whole and aligned, scalar loads otherwise.
+template <typename T>
+__device__ __forceinline__ void load_chunk(const T* __restrict__ row, int k0, int K,
+                                           T (&c)[16 / sizeof(T)]) {
+  constexpr int VE = 16 / sizeof(T);
+  const T* src = row + k0;
+  if (k0 + VE <= K && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 w = __ldg(reinterpret_cast<const float4*>(src));
+      c[0] = w.x; c[1] = w.y; c[2] = w.z; c[3] = w.w;
+    } else {
+      const double2 w = __ldg(reinterpret_cast<const double2*>(src));
+      c[0] = w.x; c[1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < VE; ++e) c[e] = k0 + e < K ? __ldg(src + e) : T(0);
+  }
+}
+
 // Euclidean projection of every pixel vector onto the probability simplex (Michelot's
 // active-set iteration: theta = (sum of the active entries - 1) / |active|, drop entries
 // <= theta, repeat; exact after at most K rounds), plus per-block partials of min z,
 // max |1^T z - 1|, sum_i -ln(p_i^T proj(z_i)) and ||G^T d||^2 (G^T d gathered from the tile
 // partials P2 in the row pass's order: covY vertical covers per row, offX per-column tile
-// offsets). G lanes per pixel, class k on lane k.
+// offsets). One pixel per thread, its G class values in registers (classes >= K are zero),
+// the active set as a bit mask.
 template <typename T, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p, T* zp, int n,
                                                         int K, const T* P2, const int* covY,
@@ -82,51 +131,70 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
                                                         int EHmax, int EWmax,
                                                         double* part /*[blocks][4]*/) {
   __shared__ double red32[32];
-  constexpr int PPB = AUX_THREADS / G;
-  const int g = threadIdx.x % G;
   T vmin = T(1e30), vdev = T(0), vdata = T(0), vgsq = T(0);
+  const uint32_t all = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
   pdl_wait();
-  for (int i0 = blockIdx.x * PPB; i0 < n; i0 += gridDim.x * PPB) {
-    const int i = i0 + threadIdx.x / G;
-    const bool ok = i < n && g < K;
-    const T v = ok ? z[(size_t)i * K + g] : T(0);
-    const T pk = ok ? p[(size_t)i * K + g] : T(0);
-    bool act = ok;
-    const T s = group_sum<G>(v);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T v[G], pk[G];
+    load_classes<T, G>(z + (size_t)i * K, K, v);
+    load_classes<T, G>(p + (size_t)i * K, K, pk);
+    T s = T(0), mn = v[0];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      s += v[k];
+      if (k < K) mn = fmin(mn, v[k]);
+    }
+    uint32_t act = all;
     T theta = T(0);
     for (int round = 0; round <= K; ++round) {
-      const T sa = group_sum<G>(act ? v : T(0));
-      const T na = group_sum<G>(act ? T(1) : T(0));
+      T sa = T(0), na = T(0);
+#pragma unroll
+      for (int k = 0; k < G; ++k)
+        if ((act >> k) & 1u) { sa += v[k]; na += T(1); }
       theta = (sa - T(1)) / fmax(na, T(1));
-      const bool nact = act && v > theta;
-      const bool changed = act && !nact;
+      uint32_t nact = 0;
+#pragma unroll
+      for (int k = 0; k < G; ++k)
+        if (((act >> k) & 1u) && v[k] > theta) nact |= 1u << k;
+      if (nact == act) break;
       act = nact;
-      if (!__any_sync(0xffffffffu, changed)) break;  // warp-uniform exit (groups share shuffles)
     }
-    const T q = ok ? fmax(v - theta, T(0)) : T(0);
-    if (ok) zp[(size_t)i * K + g] = q;
-    const T pz = group_sum<G>(pk * q);
-    if (ok) {
-      vmin = fmin(vmin, v);
-      const int y = i / W, x = i - y * W;
-      const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
-      const int rb0 = c0 < 0 ? -1 : (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
-      const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
-      const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
-      T gd = T(0);
-      if (rb0 >= 0) {
-        if (o0 >= 0) gd += P2[rb0 + o0 + g];
-        if (o1 >= 0) gd += P2[rb0 + o1 + g];
+    T pz = T(0);
+    T* zo = zp + (size_t)i * K;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const T q = fmax(v[k] - theta, T(0));
+      if (k < K) {
+        zo[k] = q;
+        pz += pk[k] * q;
       }
-      if (rb1 >= 0) {
-        if (o0 >= 0) gd += P2[rb1 + o0 + g];
-        if (o1 >= 0) gd += P2[rb1 + o1 + g];
-      }
-      vgsq += gd * gd;
     }
-    if (i < n && g == 0) {
-      vdev = fmax(vdev, fabs(s - T(1)));
-      vdata -= log(pz);
+    vmin = fmin(vmin, mn);
+    vdev = fmax(vdev, fabs(s - T(1)));
+    vdata -= log(pz);
+    // G^T d at pixel i: the (at most 2 x 2) covering partials, in the row pass's order
+    const int y = i / W, x = i - y * W;
+    const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
+    const int rb0 = (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
+    const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
+    const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
+    constexpr int VE = 16 / sizeof(T);
+#pragma unroll
+    for (int k0 = 0; k0 < G; k0 += VE) {
+      if (k0 >= K) break;
+      T g00[VE], g01[VE], g10[VE], g11[VE];
+      load_chunk<T>(P2 + rb0 + o0, k0, K, g00);
+      if (o1 >= 0) load_chunk<T>(P2 + rb0 + o1, k0, K, g01);
+      if (rb1 >= 0) load_chunk<T>(P2 + rb1 + o0, k0, K, g10);
+      if (rb1 >= 0 && o1 >= 0) load_chunk<T>(P2 + rb1 + o1, k0, K, g11);
+#pragma unroll
+      for (int e = 0; e < VE; ++e) {
+        T gd = g00[e];
+        if (o1 >= 0) gd += g01[e];
+        if (rb1 >= 0) gd += g10[e];
+        if (rb1 >= 0 && o1 >= 0) gd += g11[e];
+        vgsq += gd * gd;
+      }
     }
   }
   const double a = block_min_w<T>(vmin, red32);
@@ -139,62 +207,75 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
   if (threadIdx.x == 0) part[4 * blockIdx.x + 3] = d;
 }
 
-// sum_i ||[J zp]_i||_{S_p} per block (zp pixel-major), via the 2x2 Gram matrix of eq. (5):
-// G lanes per pixel (class k on lane k) accumulate their 2L Jacobian entries, a G-lane sum
-// gives the Gram matrix. Block sums in double.
+// sum_i ||[J zp]_i||_{S_p} per block (zp pixel-major). The Gram matrix of pixel i's patch
+// Jacobian (eq. 5) is sum_j omega_j^2 T(i + s_j), where T(m) = sum_k (grad z_k)(grad z_k)^T
+// at pixel m (forward differences): the structure tensor of Sec. 3. A block takes tiles of
+// PRIOR_TH x PRIOR_TW pixels: it first forms the three entries of T on the tile and its
+// M-pixel halo in shared memory (one pixel per thread, classes in registers), then every
+// pixel sums the L weighted taps and takes the norm from the two eigenvalues.
+constexpr int PRIOR_TH = 8, PRIOR_TW = 32;  // PRIOR_TH * PRIOR_TW == AUX_THREADS
 template <typename T, int M, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* omega, int H, int W,
                                                       int K, int sp, double* part) {
-  __shared__ double red32[32];
-  constexpr int PPB = AUX_THREADS / G;
   constexpr int P = 2 * M + 1;
-  const int g = threadIdx.x % G;
-  const int n = H * W;
+  constexpr int RH = PRIOR_TH + 2 * M, RW = PRIOR_TW + 2 * M;
+  __shared__ double red32[32];
+  __shared__ T sA[RH * RW], sB[RH * RW], sC[RH * RW];
+  __shared__ T w2[P * P];
+  for (int j = threadIdx.x; j < P * P; j += blockDim.x) w2[j] = omega[j] * omega[j];
+  const int ntx = (W + PRIOR_TW - 1) / PRIOR_TW;
+  const int ntiles = ((H + PRIOR_TH - 1) / PRIOR_TH) * ntx;
   T val = T(0);
   pdl_wait();
-  for (int i0 = blockIdx.x * PPB; i0 < n; i0 += gridDim.x * PPB) {
-    const int i = i0 + threadIdx.x / G;
-    const bool ok = i < n && g < K;
-    const int y = ok ? i / W : 0, x = ok ? i % W : 0;
-    T zv[P + 1][P + 1];
-    int xs[P + 1];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int y0 = (tile / ntx) * PRIOR_TH, x0 = (tile % ntx) * PRIOR_TW;
+    __syncthreads();  // the previous tile's reads of sA/sB/sC are done (and w2 is written)
+    for (int r = threadIdx.x; r < RH * RW; r += blockDim.x) {
+      const int ry = r / RW, rx = r - ry * RW;
+      const int y = wrap_idx(y0 - M + ry, H), x = wrap_idx(x0 - M + rx, W);
+      const int xh = x + 1 == W ? 0 : x + 1, yv = y + 1 == H ? 0 : y + 1;
+      constexpr int VE = 16 / sizeof(T);
+      const T* rc = zp + ((size_t)y * W + x) * K;
+      const T* rh = zp + ((size_t)y * W + xh) * K;
+      const T* rv = zp + ((size_t)yv * W + x) * K;
+      T a = T(0), b = T(0), c = T(0);
 #pragma unroll
-    for (int dx = 0; dx <= P; ++dx) {
-      int xx = x - M + dx;
-      xx += (xx < 0) ? W : 0;
-      xx -= (xx >= W) ? W : 0;
-      xs[dx] = xx;
-    }
+      for (int k0 = 0; k0 < G; k0 += VE) {
+        if (k0 >= K) break;
+        T zc[VE], zh[VE], zv[VE];
+        load_chunk<T>(rc, k0, K, zc);
+        load_chunk<T>(rh, k0, K, zh);
+        load_chunk<T>(rv, k0, K, zv);
 #pragma unroll
-    for (int dy = 0; dy <= P; ++dy) {
-      int yy = y - M + dy;
-      yy += (yy < 0) ? H : 0;
-      yy -= (yy >= H) ? H : 0;
-      const size_t row = (size_t)yy * W;
-#pragma unroll
-      for (int dx = 0; dx <= P; ++dx)
-        zv[dy][dx] = (ok && !(dy == P && dx == P)) ? zp[(row + xs[dx]) * K + g] : T(0);
-    }
-    T a = T(0), b = T(0), c = T(0);
-#pragma unroll
-    for (int dy = 0; dy < P; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < P; ++dx) {
-        const T w = omega[dy * P + dx];
-        const T h = w * (zv[dy][dx + 1] - zv[dy][dx]);
-        const T v = w * (zv[dy + 1][dx] - zv[dy][dx]);
-        a += h * h;
-        b += h * v;
-        c += v * v;
+        for (int e = 0; e < VE; ++e) {
+          const T h = zh[e] - zc[e], v = zv[e] - zc[e];
+          a += h * h;
+          b += h * v;
+          c += v * v;
+        }
       }
-    a = group_sum<G>(a);
-    b = group_sum<G>(b);
-    c = group_sum<G>(c);
-    if (i < n && g == 0) {
+      sA[r] = a;
+      sB[r] = b;
+      sC[r] = c;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / PRIOR_TW, tx = threadIdx.x - ty * PRIOR_TW;
+    if (y0 + ty < H && x0 + tx < W) {
+      T a = T(0), b = T(0), c = T(0);
+#pragma unroll
+      for (int dy = 0; dy < P; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < P; ++dx) {
+          const T w = w2[dy * P + dx];
+          const int r = (ty + dy) * RW + tx + dx;
+          a += w * sA[r];
+          b += w * sB[r];
+          c += w * sC[r];
+        }
       const T hd = T(0.5) * (a - c);
-      const T r = sqrt(hd * hd + b * b);
-      const T s1 = sqrt(fmax(T(0.5) * (a + c) + r, T(0)));
-      const T s2 = sqrt(fmax(T(0.5) * (a + c) - r, T(0)));
+      const T rr = sqrt(hd * hd + b * b);
+      const T s1 = sqrt(fmax(T(0.5) * (a + c) + rr, T(0)));
+      const T s2 = sqrt(fmax(T(0.5) * (a + c) - rr, T(0)));
       val += (sp == 1) ? s1 + s2 : (sp == 2) ? sqrt(fmax(a + c, T(0))) : s1;
     }
   }

@@ -321,11 +321,14 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
     }
   }
   // diagnostics
-  const int cap = 152 * 16;
-  const int ppb = AUX_THREADS / pl.G;  // pixels per diagnostics block
-  // at least four grid-stride rounds per block, at most 16 blocks per SM
-  pl.nproj_blk = std::max(1, std::min(cap, (pl.n + 4 * ppb - 1) / (4 * ppb)));
-  pl.nprior_blk = pl.nproj_blk;
+  // one pixel per thread (projection) and tiles of PRIOR_TH x PRIOR_TW pixels (prior): at least
+  // four grid-stride rounds per block, at most eight blocks per SM
+  const int cap = 152 * 8;
+  pl.nproj_blk = std::max(1, std::min(cap, (pl.n + 4 * AUX_THREADS - 1) / (4 * AUX_THREADS)));
+  {
+    const int pt = ((H + PRIOR_TH - 1) / PRIOR_TH) * ((W + PRIOR_TW - 1) / PRIOR_TW);
+    pl.nprior_blk = std::max(1, std::min(cap, (pt + 3) / 4));
+  }
   return SEGSALSA_OK;
 }
 
