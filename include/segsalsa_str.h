@@ -69,8 +69,12 @@ enum { SEGSALSA_G4_AFFINE = 0, SEGSALSA_G4_SIMPLEX = 1 }; /* segsalsa_str_set_g4
 typedef struct {
   int32_t H, W;          /* image size; H, W >= 2M+2                                      */
   int32_t K;             /* number of classes, 2 <= K <= 32                               */
-  int32_t M;             /* patch half-width: (2M+1)x(2M+1) patch, 0 <= M <= 2.
-                            M = 0 is the 1x1 patch, i.e. SegSALSA with the VTV prior (Sec. 3) */
+  int32_t M;             /* patch half-width: (2M+1)x(2M+1) patch, 0 <= M <= 5 (1x1 up to
+                            the 11x11 patch of Sec. 5's patch-size study). M = 0 is the 1x1
+                            patch, i.e. SegSALSA with the VTV prior (Sec. 3). M <= 2 runs the
+                            fused one-launch sweep; M >= 3 a two-launch sweep (per-pixel Gram
+                            matrix and prox coefficients, then J^T as a gather) that needs a
+                            second d2-sized buffer for u2 + d2 (see workspace_bytes)        */
   const double* weights; /* L = (2M+1)^2 shift weights omega_j (row-major over (dy, dx)),
                             host memory, copied at creation; NULL selects the Gaussian
                             omega_j = sqrt(g_j), g_j = exp(-|s_j|^2/(2 sigma^2)) / sum        */
@@ -169,7 +173,8 @@ int segsalsa_str_set_weights(segsalsa_str_t* h, const double* weights);
  * Jacobians applied per pixel, and the adjoint of J is J^T. Device memory for the checkpoints
  * and one segment's states is allocated for the call and released before it returns. The
  * handle ends at iteration `iters`, as after set_probs + solve(iters).
- * Covers Schatten p = 1 and 2 with g4 on the affine set; SEGSALSA_ERR_ARG otherwise. The
+ * Covers Schatten p = 1 and 2 with g4 on the affine set and patches up to 5x5 (M <= 2);
+ * SEGSALSA_ERR_ARG otherwise. The
  * derivative is that of the iteration as written: at points where an MPO switches case (a
  * singular value equal to tau, a component of v3 equal to 0) one side's derivative is taken. */
 int segsalsa_str_backward(segsalsa_str_t* h, int32_t iters, const void* zbar, int32_t layout,

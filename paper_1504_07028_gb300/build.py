@@ -17,7 +17,7 @@ LIB = os.path.join(LIBDIR, "libsegsalsa_str.so")
 
 SOURCES = ["solver.cu", "sweep_f32.cu", "sweep_f64.cu", "sweep_f32_keq.cu", "sweep_f64_keq.cu",
            "sweep_f32_simplex.cu", "sweep_f64_simplex.cu", "fft_f32.cu", "fft_f64.cu", "noalloc.cu",
-           "mlr.cu", "adjoint.cu"]
+           "mlr.cu", "adjoint.cu", "wide_f32.cu", "wide_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

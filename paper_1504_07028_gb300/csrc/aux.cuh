@@ -122,11 +122,12 @@ __device__ __forceinline__ void load_chunk(const T* __restrict__ row, int k0, in
 // <= theta, repeat; exact after at most K rounds), plus per-block partials of min z,
 // max |1^T z - 1|, sum_i -ln(p_i^T proj(z_i)) and ||G^T d||^2 (G^T d gathered from the tile
 // partials P2 in the row pass's order: covY vertical covers per row, offX per-column tile
-// offsets). One pixel per thread, its G class values in registers (classes >= K are zero),
-// the active set as a bit mask.
+// offsets; or read from the dense gtd [n][K] when it is given). One pixel per thread, its G
+// class values in registers (classes >= K are zero), the active set as a bit mask.
 template <typename T, int G>
 __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p, T* zp, int n,
-                                                        int K, const T* P2, const int* covY,
+                                                        int K, const T* P2, const T* gtd,
+                                                        const int* covY,
                                                         const int* offX, int W, int ntx,
                                                         int EHmax, int EWmax,
                                                         double* part /*[blocks][4]*/) {
@@ -172,13 +173,24 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
     vmin = fmin(vmin, mn);
     vdev = fmax(vdev, fabs(s - T(1)));
     vdata -= log(pz);
+    constexpr int VE = 16 / sizeof(T);
+    if (gtd) {
+#pragma unroll
+      for (int k0 = 0; k0 < G; k0 += VE) {
+        if (k0 >= K) break;
+        T gd[VE];
+        load_chunk<T>(gtd + (size_t)i * K, k0, K, gd);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) vgsq += gd[e] * gd[e];
+      }
+      continue;
+    }
     // G^T d at pixel i: the (at most 2 x 2) covering partials, in the row pass's order
     const int y = i / W, x = i - y * W;
     const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
     const int rb0 = (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
     const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
     const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
-    constexpr int VE = 16 / sizeof(T);
 #pragma unroll
     for (int k0 = 0; k0 < G; k0 += VE) {
       if (k0 >= K) break;
@@ -285,21 +297,21 @@ __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* ome
 
 template <typename T, int G>
 inline void launch_project(int blocks, cudaStream_t st, const T* z, const T* p, T* zp, int n,
-                           int K, const T* P2, const int* covY, const int* offX, int W, int ntx,
-                           int EHmax, int EWmax, double* part) {
-  launch_pdl(k_project<T, G>, dim3(blocks), dim3(AUX_THREADS), 0, st, z, p, zp, n, K, P2, covY,
-             offX, W, ntx, EHmax, EWmax, part);
+                           int K, const T* P2, const T* gtd, const int* covY, const int* offX,
+                           int W, int ntx, int EHmax, int EWmax, double* part) {
+  launch_pdl(k_project<T, G>, dim3(blocks), dim3(AUX_THREADS), 0, st, z, p, zp, n, K, P2, gtd,
+             covY, offX, W, ntx, EHmax, EWmax, part);
 }
 template <typename T>
 inline cudaError_t launch_project_g(int G, int blocks, cudaStream_t st, const T* z, const T* p,
-                                    T* zp, int n, int K, const T* P2, const int* covY,
-                                    const int* offX, int W, int ntx, int EHmax, int EWmax,
-                                    double* part) {
+                                    T* zp, int n, int K, const T* P2, const T* gtd,
+                                    const int* covY, const int* offX, int W, int ntx, int EHmax,
+                                    int EWmax, double* part) {
   switch (G) {
-    case 4: launch_project<T, 4>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
-    case 8: launch_project<T, 8>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
-    case 16: launch_project<T, 16>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
-    default: launch_project<T, 32>(blocks, st, z, p, zp, n, K, P2, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    case 4: launch_project<T, 4>(blocks, st, z, p, zp, n, K, P2, gtd, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    case 8: launch_project<T, 8>(blocks, st, z, p, zp, n, K, P2, gtd, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    case 16: launch_project<T, 16>(blocks, st, z, p, zp, n, K, P2, gtd, covY, offX, W, ntx, EHmax, EWmax, part); break;
+    default: launch_project<T, 32>(blocks, st, z, p, zp, n, K, P2, gtd, covY, offX, W, ntx, EHmax, EWmax, part); break;
   }
   return cudaGetLastError();
 }
@@ -319,7 +331,10 @@ inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const
   switch (M) {
     case 0: launch_prior_m<T, 0>(G, blocks, st, zp, om, H, W, K, sp, part); break;
     case 1: launch_prior_m<T, 1>(G, blocks, st, zp, om, H, W, K, sp, part); break;
-    default: launch_prior_m<T, 2>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    case 2: launch_prior_m<T, 2>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    case 3: launch_prior_m<T, 3>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    case 4: launch_prior_m<T, 4>(G, blocks, st, zp, om, H, W, K, sp, part); break;
+    default: launch_prior_m<T, 5>(G, blocks, st, zp, om, H, W, K, sp, part); break;
   }
   return cudaGetLastError();
 }

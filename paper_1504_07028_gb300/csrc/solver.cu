@@ -27,6 +27,7 @@
 #include "launch.h"
 #include "mlr.cuh"
 #include "adjoint.cuh"
+#include "wide.cuh"
 
 namespace sgs {
 
@@ -84,7 +85,7 @@ struct SolverBase {
 // Validation of the parameters shared by create and workspace_bytes.
 static int check_params(const segsalsa_str_params* pr, std::string& msg) {
   if (!pr) { msg = "params is NULL"; return SEGSALSA_ERR_ARG; }
-  if (pr->M < 0 || pr->M > 2) { msg = "M must be 0, 1 or 2"; return SEGSALSA_ERR_ARG; }
+  if (pr->M < 0 || pr->M > 5) { msg = "M must be in [0, 5]"; return SEGSALSA_ERR_ARG; }
   if (pr->K < 2 || pr->K > 32) { msg = "K must be in [2, 32]"; return SEGSALSA_ERR_ARG; }
   const int minsz = 2 * pr->M + 2;
   if (pr->H < minsz || pr->W < minsz) { msg = "H and W must be >= 2M+2"; return SEGSALSA_ERR_ARG; }
@@ -146,6 +147,8 @@ struct Plan {
   int zf_cs, zf_qg, zf_rmax, zf_groups, zf_threads;
   size_t zf_smem;
   int nproj_blk, nprior_blk;
+  // wide patches (M >= 3): two-launch sweep (gram + transpose tiles) writing a dense rhs
+  int wide, wntx1, wntiles1, wnblk2;
   std::vector<int> covY, covX;  // [H][MAXCOV], [W][MAXCOV]
 };
 
@@ -224,10 +227,27 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.EWmax = pl.NC + 2 * M + 1;
   pl.sweep_smem = sweep_smem_bytes<T>(pl.NC, pl.EHmax, pl.EWmax, pl.G, pl.L, K, false);
   pl.sweep_smem_diag = sweep_smem_bytes<T>(pl.NC, pl.EHmax, pl.EWmax, pl.G, pl.L, K, true);
-  if (pl.sweep_smem_diag > 227 * 1024) { msg = "tile does not fit in shared memory"; return SEGSALSA_ERR_ARG; }
+  pl.wide = M >= 3;
+  pl.wntx1 = (W + 256 / pl.G - 1) / (256 / pl.G);
+  pl.wntiles1 = pl.wntx1 * ((H + WG_TH - 1) / WG_TH);
+  // transpose: 256 / G pixels per block and round, at least four rounds, at most 8 blocks / SM
+  pl.wnblk2 = std::max(1, std::min(152 * 8, (pl.n + 4 * (256 / pl.G) - 1) / (4 * (256 / pl.G))));
+  if (pl.wide) {
+    if (wide_gram_smem<T>(M, pl.G) > 227 * 1024) {
+      msg = "wide-patch tiles do not fit in shared memory"; return SEGSALSA_ERR_ARG;
+    }
+  } else if (pl.sweep_smem_diag > 227 * 1024) {
+    msg = "tile does not fit in shared memory"; return SEGSALSA_ERR_ARG;
+  }
   pl.ntiles = pl.ntx * pl.nty;
   if ((long long)pl.ntiles * pl.EHmax * pl.EWmax * K >= (1LL << 31)) { msg = "image too large for 32-bit partial offsets"; return SEGSALSA_ERR_ARG; }
-  if (!build_cover(H, pl.nty, M, M + 1, pl.covY) || !build_cover(W, pl.ntx, M, M + 1, pl.covX)) {
+  if (M >= 3) {
+    // the wide-patch sweep writes a dense rhs: no tile partials to gather (trivial covers)
+    pl.covY.assign((size_t)H * MAXCOV, -1);
+    pl.covX.assign((size_t)W * MAXCOV, -1);
+    for (int y = 0; y < H; ++y) pl.covY[(size_t)y * MAXCOV] = 0;
+    for (int x = 0; x < W; ++x) pl.covX[(size_t)x * MAXCOV] = 0;
+  } else if (!build_cover(H, pl.nty, M, M + 1, pl.covY) || !build_cover(W, pl.ntx, M, M + 1, pl.covX)) {
     msg = "image too small for the tiling"; return SEGSALSA_ERR_ARG;
   }
   // row FFT
@@ -347,6 +367,7 @@ struct Carver {
 template <typename T>
 struct Buffers {
   T *p, *z, *dloc, *d2, *P, *P2, *zp, *tmp, *rhsd;
+  T* wbuf;  // wide patches: omega_j (u2 + d2) of the last sweep, [n][L][K][2]
   cplx<T>* S;
   int32_t* lab;
   double *dsq, *dproj, *dprior, *dtrace;
@@ -375,8 +396,9 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.tmp = c.take<T>(nK);
   b.rhsd = c.take<T>(nK);
   b.S = c.take<cplx<T>>((size_t)pl.H * pl.Wh * pl.K);
+  b.wbuf = pl.wide ? c.take<T>(2 * (size_t)pl.L * nK) : nullptr;
   b.lab = c.take<int32_t>(pl.n);
-  b.dsq = c.take<double>(pl.ntiles);
+  b.dsq = c.take<double>(std::max(pl.ntiles, pl.wntiles1));
   b.dproj = c.take<double>(4 * (size_t)pl.nproj_blk);
   b.dprior = c.take<double>(pl.nprior_blk);
   b.dtrace = c.take<double>(6 * (size_t)TRACE_CAP);
@@ -476,7 +498,8 @@ class Solver : public SolverBase {
     carve<T>(pl, reinterpret_cast<char*>(ws), b);
     if (pr->stream) st = reinterpret_cast<cudaStream_t>(pr->stream);
     else { SGS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
-    if (pl.K == pl.G && pl.NC == 256 / pl.G) SGS_CUDA(prepare_sweep_keq<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
+    if (pl.wide) SGS_CUDA(prepare_wide<T>(pl.M, pl.G));
+    else if (pl.K == pl.G && pl.NC == 256 / pl.G) SGS_CUDA(prepare_sweep_keq<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     else SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
     if (pl.zf_cs && zfused_max_clusters<T>(pl.zf_cs, pl.zf_threads, pl.zf_smem) < 1) pl.zf_cs = 0;
@@ -611,8 +634,10 @@ class Solver : public SolverBase {
     return a;
   }
 
-  // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep partials (src == nullptr)
+  // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep's rhs (src == nullptr: the tile
+  // partials, or the dense rhs of the wide-patch sweep)
   int z_update(const T* src, T* zout) {
+    if (!src && pl.wide) src = b.rhsd;
     const RowArgs<T> ra = row_args(src, zout);
     if (pl.zf_cs) {
       ZfArgs<T> za{};
@@ -641,6 +666,20 @@ class Solver : public SolverBase {
   }
 
   int sweep(bool diag) {
+    if (pl.wide) {
+      WideArgs<T> w{};
+      w.H = pl.H; w.W = pl.W; w.K = pl.K; w.M = pl.M; w.L = pl.L;
+      w.z = b.z; w.p = b.p; w.dloc = b.dloc; w.d2 = b.d2; w.wbuf = b.wbuf; w.rhs = b.rhsd;
+      w.gtd = b.P2; w.diag_sq = b.dsq; w.omega = b.omega;
+      w.tau = (T)(lambda / mu); w.mu = (T)mu; w.invK = (T)(1.0 / pl.K); w.sp = sp;
+      w.ntx1 = pl.wntx1; w.ntiles1 = pl.wntiles1; w.nblk2 = pl.wnblk2;
+      // two kernels per sweep; counted as one sweep launch each
+      nlaunch[KIND_SWEEP]++;
+      SGS_CUDA(launch(KIND_SWEEP, [&]() {
+        return launch_wide<T>(w, pl.G, diag, g4 == SEGSALSA_G4_SIMPLEX, st);
+      }));
+      return SEGSALSA_OK;
+    }
     SweepArgs<T> a{};
     a.H = pl.H; a.W = pl.W; a.K = pl.K; a.NC = pl.NC; a.ntx = pl.ntx; a.nty = pl.nty;
     a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
@@ -661,9 +700,9 @@ class Solver : public SolverBase {
 
   int diagnostics(int k, int rec) {
     const int n = pl.n, K = pl.K;
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, (const T*)b.P2, (const int*)b.covY, (const int*)b.offX, pl.W, pl.ntx, pl.EHmax, pl.EWmax, b.dproj); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, (const T*)b.P2, pl.wide ? (const T*)b.P2 : nullptr, (const int*)b.covY, (const int*)b.offX, pl.W, pl.ntx, pl.EHmax, pl.EWmax, b.dproj); }));
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_prior<T>(pl.M, pl.G, pl.nprior_blk, st, b.zp, b.omega, pl.H, pl.W, K, sp, b.dprior); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(32), 0, st, (const double*)b.dsq, pl.ntiles, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(32), 0, st, (const double*)b.dsq, pl.wide ? pl.wntiles1 : pl.ntiles, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
     return SEGSALSA_OK;
   }
 
@@ -954,7 +993,7 @@ class Solver : public SolverBase {
       SGS_CUDA(cudaStreamSynchronize(st));
     }
     if (rhs) {
-      if (rhs_dense) {
+      if (rhs_dense || pl.wide) {
         if ((rc = copy_out(rhs, b.rhsd, nK, dev))) return rc;
       } else {
         const RowArgs<T> ra = row_args(nullptr, b.tmp);
@@ -1104,7 +1143,7 @@ class Solver : public SolverBase {
   int set_g4(int mode) override {
     if (mode != SEGSALSA_G4_AFFINE && mode != SEGSALSA_G4_SIMPLEX) return fail(SEGSALSA_ERR_ARG, "bad g4 mode");
     if (mode == g4) return SEGSALSA_OK;
-    if (mode == SEGSALSA_G4_SIMPLEX)
+    if (mode == SEGSALSA_G4_SIMPLEX && !pl.wide)  // the wide kernels are prepared at create
       SGS_CUDA(prepare_sweep_simplex<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(cudaStreamSynchronize(st));
     for (auto& kv : chunks)
@@ -1168,6 +1207,7 @@ class Solver : public SolverBase {
     if (!zbar || !glogp) return fail(SEGSALSA_ERR_ARG, "zbar and grad_logp are required");
     if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
     if (sp == 0) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers Schatten p = 1 and 2");
+    if (pl.wide) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers patches up to 5 x 5 (M <= 2)");
     if (g4 != SEGSALSA_G4_AFFINE) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers g4 on the affine set");
     const int K = pl.K, L = pl.L, n = pl.n;
     const size_t nK = (size_t)n * K, nloc = 3 * nK, n2 = 2 * (size_t)L * nK;

@@ -43,7 +43,9 @@ def test_params_struct_matches_header():
 
 @pytest.mark.parametrize("kw,ok", [
     (dict(H=145, W=145, K=16), True), (dict(H=3, W=3, K=4), False), (dict(H=8, W=8, K=1), False),
-    (dict(H=8, W=8, K=33), False), (dict(H=8, W=8, K=4, M=3), False),
+    (dict(H=8, W=8, K=33), False), (dict(H=8, W=8, K=4, M=3), True),
+    (dict(H=12, W=12, K=4, M=5), True), (dict(H=11, W=12, K=4, M=5), False),
+    (dict(H=16, W=16, K=4, M=6), False),
     (dict(H=8, W=8, K=4, lam=-1.0), False), (dict(H=8, W=8, K=4, mu=0.0), False),
     (dict(H=8, W=8, K=4, schatten_p=3), False), (dict(H=8, W=8, K=4, sigma=0.0), False),
     (dict(H=2, W=2, K=4, M=0), True), (dict(H=2048, W=2048, K=16), True),
