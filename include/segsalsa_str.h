@@ -295,8 +295,11 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
  *   row_pipe    : form of the two row-transform passes: 1 = one CTA per (row, class block);
  *                 2 = persistent CTAs (one wave) that walk the (row, class block) units and
  *                 copy the next unit's input into shared memory asynchronously while the
- *                 current unit is transformed; 0 = the library's choice. Both forms give
- *                 the same results. */
+ *                 current unit is transformed; 3 = power-of-two rows (W = 256 ... 4096, no
+ *                 Bluestein, K a multiple of 2 row_pairs): compile-time transform plan with
+ *                 the first stage computed straight from the loaded row (rows that do not
+ *                 qualify run form 1); 0 = the library's choice (3 where it applies, else 1).
+ *                 All forms give the same results. */
 typedef struct {
   int32_t tile_rows;
   int32_t row_pairs;

@@ -1112,6 +1112,255 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   }
 }
 
+// ------------------------------------------- power-of-two rows, compile-time Stockham plan
+//
+// Rows of N = 2^LOGN (256 <= N <= 4096) with B = QB class pairs per CTA whose 2B classes are
+// whole 16- or 8-byte vectors: the plan of make_fft_plan (radix-8 stages, then one radix-4 or
+// radix-2 stage) with every size, stride and twiddle step a compile-time constant, and the
+// first radix-8 stage computed in registers straight from the loaded row (the gather of the
+// rhs partials, or the Hermitian extension of the spectrum) instead of going through shared
+// memory first. Same stages, same twiddles, same operation order as the generic kernels: the
+// results are identical.
+
+template <int LOGN>
+struct P2Plan {
+  static constexpr int N = 1 << LOGN;
+};
+
+// One Stockham stage of radix R with Ns = NS on B interleaved sequences (generic fft_stage
+// with compile-time arguments).
+template <typename T, int N, int B, int R, int NS>
+__device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T>* __restrict__ Xout,
+                                         const cplx<T>* tw) {
+  using C = cplx<T>;
+  constexpr int NB = N / R;
+  constexpr int ITEMS = NB * B;
+  constexpr int STRIDE = NB / NS;
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int t = it / B, b = it - t * B;
+    const int g = t / NS;
+    const int j = t - g * NS;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * NB) * B + b)];
+    if constexpr (NS > 1) {
+      const C w1 = tw[j * STRIDE];
+      v[1] = cmul(v[1], w1);
+      if constexpr (R > 2) {
+        const C w2 = cmul(w1, w1);
+        v[2] = cmul(v[2], w2);
+        if constexpr (R > 3) {
+          const C w3 = cmul(w2, w1);
+          v[3] = cmul(v[3], w3);
+          if constexpr (R > 4) {
+            const C w4 = tw[4 * j * STRIDE];
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], cmul(w4, w1));
+            v[6] = cmul(v[6], cmul(w4, w2));
+            v[7] = cmul(v[7], cmul(w4, w3));
+          }
+        }
+      }
+    }
+    Dft<R, C>::run(v);
+    const int base = (g * NS * R + j) * B + b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) Xout[px<T>(base + r * NS * B)] = v[r];
+  }
+}
+
+// The stages after the first (Ns = NS onwards), ping-ponging; returns the result buffer.
+template <typename T, int N, int B, int NS>
+__device__ __forceinline__ cplx<T>* p2_rest(cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
+  if constexpr (NS == N) {
+    return in;
+  } else {
+    constexpr int R = (N / NS >= 8) ? 8 : (N / NS == 4 ? 4 : 2);
+    p2_stage<T, N, B, R, NS>(in, out, tw);
+    __syncthreads();
+    return p2_rest<T, N, B, NS * R>(out, in, tw);
+  }
+}
+
+// First stage (radix 8, Ns = 1, no twiddles) of sequence b of butterfly t from registers.
+template <typename T, int N, int B>
+__device__ __forceinline__ void p2_first(cplx<T> (&v)[8], int t, int b, cplx<T>* Xout) {
+  Dft<8, cplx<T>>::run(v);
+  const int base = t * 8 * B + b;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) Xout[px<T>(base + r * B)] = v[r];
+}
+
+// 2B consecutive values of type T (one class block of a pixel) as complex pairs.
+template <typename T, int B>
+__device__ __forceinline__ void p2_load_block(const T* __restrict__ src, cplx<T> (&c)[B]) {
+  if constexpr (sizeof(T) * 2 * B >= 16) {
+    constexpr int NV = sizeof(T) * 2 * B / 16;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src) + v);
+        c[2 * v] = mkc<T>(q.x, q.y);
+        c[2 * v + 1] = mkc<T>(q.z, q.w);
+      } else {
+        const double2 q = __ldg(reinterpret_cast<const double2*>(src) + v);
+        c[v] = mkc<T>(q.x, q.y);
+      }
+    }
+  } else {  // FP32, B = 1: one 8-byte pair
+    const float2 q = __ldg(reinterpret_cast<const float2*>(src));
+    c[0] = mkc<T>(q.x, q.y);
+  }
+}
+
+// Threads of a power-of-two row CTA: one first-stage butterfly of one sequence each.
+template <int LOGN, int B>
+constexpr int p2_threads() {
+  return ((1 << LOGN) / 8 * B) > 512 ? 512 : ((1 << LOGN) / 8 * B);
+}
+
+template <typename T, int LOGN, int B>
+__global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const RowArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int N = 1 << LOGN;
+  constexpr int NB = N / 8;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* X = reinterpret_cast<C*>(smem_raw);
+  C* Y = X + padded_elems<T>((size_t)N * B);
+  const int y = blockIdx.y;
+  const int q0 = blockIdx.x * B;
+  const int c0 = 2 * q0;
+  const C* tw = a.pl.tw;
+  pdl_wait();  // rhs / partials come from the previous kernel
+  const int rb0 = a.src ? -1 : cover_row_base(a, a.covY[2 * y]);
+  const int rb1 = a.src ? -1 : cover_row_base(a, a.covY[2 * y + 1]);
+  const bool hy = rb1 >= 0;
+  for (int it = threadIdx.x; it < NB * B; it += blockDim.x) {
+    const int t = it / B, q = it - t * B;
+    const int cq = c0 + 2 * q;              // the pair's classes cq, cq + 1
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int x = t + r * NB;
+      C c[1];
+      if (a.src) {
+        p2_load_block<T, 1>(a.src + ((size_t)y * N + x) * a.K + cq, c);
+      } else {
+        // p00 (+ p01) (+ p10) (+ p11), the order of gather_row16; absent covers not loaded
+        const int2 ox = __ldg(reinterpret_cast<const int2*>(a.offX) + x);
+        const bool hx = ox.y >= 0;
+        p2_load_block<T, 1>(a.P + rb0 + ox.x + cq, c);
+        C e[1];
+        if (hx) {
+          p2_load_block<T, 1>(a.P + rb0 + ox.y + cq, e);
+          c[0] = cadd(c[0], e[0]);
+        }
+        if (hy) {
+          p2_load_block<T, 1>(a.P + rb1 + ox.x + cq, e);
+          c[0] = cadd(c[0], e[0]);
+          if (hx) {
+            p2_load_block<T, 1>(a.P + rb1 + ox.y + cq, e);
+            c[0] = cadd(c[0], e[0]);
+          }
+        }
+      }
+      v[r] = c[0];
+    }
+    p2_first<T, N, B>(v, t, q, Y);
+  }
+  __syncthreads();
+  const C* R = p2_rest<T, N, B, 8>(Y, X, tw);
+  pdl_trigger();
+  // unpack the two real spectra of each pair (as k_row_forward)
+  for (int i = threadIdx.x; i < (N / 2 + 1) * B; i += blockDim.x) {
+    const int qq = i % B;
+    const int kx = i / B;
+    const C u = R[px<T>(kx * B + qq)];
+    const C w = R[px<T>(((kx == 0) ? 0 : N - kx) * B + qq)];
+    C oa, ob;
+    oa.x = T(0.5) * (u.x + w.x); oa.y = T(0.5) * (u.y - w.y);
+    ob.x = T(0.5) * (u.y + w.y); ob.y = T(0.5) * (w.x - u.x);
+    store_pair(a.S + ((size_t)y * a.Wh + kx) * a.K + 2 * (q0 + qq), oa, ob);
+  }
+}
+
+template <typename T, int LOGN, int B>
+__global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_inverse_p2(const RowArgs<T> a) {
+  using C = cplx<T>;
+  constexpr int N = 1 << LOGN;
+  constexpr int NB = N / 8;
+  constexpr int WH = N / 2 + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* X = reinterpret_cast<C*>(smem_raw);
+  C* Y = X + padded_elems<T>((size_t)N * B);
+  const int y = blockIdx.y;
+  const int q0 = blockIdx.x * B;
+  const C* tw = a.pl.tw;
+  pdl_wait();  // the spectrum comes from the column pass
+  for (int it = threadIdx.x; it < NB * B; it += blockDim.x) {
+    const int t = it / B, q = it - t * B;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int kx = t + r * NB;
+      const int ks = kx < WH ? kx : N - kx;
+      C A, Bq;
+      load_pair(a.S + ((size_t)y * WH + ks) * a.K + 2 * (q0 + q), A, Bq);
+      if (kx >= WH) { A = cconj(A); Bq = cconj(Bq); }
+      C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);   // conj(A + i B)
+      v[r] = xv;
+    }
+    p2_first<T, N, B>(v, t, q, Y);
+  }
+  __syncthreads();
+  const C* R = p2_rest<T, N, B, 8>(Y, X, tw);
+  pdl_trigger();
+  const T inv = T(1) / T(N);
+  constexpr int VE = 16 / sizeof(T);
+  if constexpr ((2 * B) % VE == 0) {
+    constexpr int NV = 2 * B / VE;
+    for (int i = threadIdx.x; i < N * NV; i += blockDim.x) {
+      const int x = i / NV, j = i - x * NV;
+      T o[VE];
+#pragma unroll
+      for (int e = 0; e < VE / 2; ++e) {
+        const C v = R[px<T>(x * B + j * (VE / 2) + e)];   // conj(v) / N
+        o[2 * e] = v.x * inv;
+        o[2 * e + 1] = -v.y * inv;
+      }
+      T* dst = a.z + ((size_t)y * N + x) * a.K + 2 * q0 + j * VE;
+      if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+      else
+        *reinterpret_cast<double2*>(dst) = make_double2(o[0], o[1]);
+    }
+  } else {  // FP32, B = 1: 8-byte stores
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+      const C v = R[px<T>(x)];
+      *reinterpret_cast<float2*>(a.z + ((size_t)y * N + x) * a.K + 2 * q0) =
+          make_float2(v.x * inv, -v.y * inv);
+    }
+  }
+}
+
+// Whether a row plan can run the power-of-two kernels: N = 2^LOGN with 256 <= N <= 4096, no
+// Bluestein, B in {1, 2, 4}, every class block whole (K a multiple of 2B) and the caller's
+// dense buffers (when used) aligned to the block's vector size.
+inline int p2_log2(int N) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return (1 << l) == N ? l : -1;
+}
+template <typename T>
+inline bool p2_ok(int N, int blue, int QB, int K) {
+  const int l = p2_log2(N);
+  return !blue && l >= 8 && l <= 12 && (QB == 1 || QB == 2 || QB == 4) && K % (2 * QB) == 0;
+}
+template <typename T>
+inline size_t p2_smem_bytes(int N, int QB) {
+  return sizeof(cplx<T>) * 2 * padded_elems<T>((size_t)N * QB);
+}
+
 // ---------------------------------------------------------------- host-side launch helpers
 struct RowLaunch {
   int threads;
@@ -1258,6 +1507,10 @@ cudaError_t launch_row_pipe(bool forward, const RowArgs<T>& a, int grid, size_t 
                             cudaStream_t st);
 template <typename T>
 cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks);
+// Power-of-two row passes (p2_ok): grid (class blocks, rows), N / 8 * QB threads (<= 512).
+template <typename T>
+cudaError_t launch_row_p2(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
+                          cudaStream_t st);
 
 
 #ifdef SGS_FFT_INSTANTIATE
@@ -1334,6 +1587,51 @@ cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks) {
                                                        ROWPIPE_THREADS, smem);
 }
 
+template <typename T, int LOGN, int B>
+struct RowP2Grant {
+  static SmemGrants f, i;
+};
+template <typename T, int LOGN, int B> SmemGrants RowP2Grant<T, LOGN, B>::f;
+template <typename T, int LOGN, int B> SmemGrants RowP2Grant<T, LOGN, B>::i;
+
+template <typename T, int LOGN, int B>
+cudaError_t launch_row_p2_inst(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
+                               cudaStream_t st) {
+  cudaError_t e;
+  if (forward) {
+    if ((e = grant_smem(k_row_forward_p2<T, LOGN, B>, smem, RowP2Grant<T, LOGN, B>::f)) != cudaSuccess)
+      return e;
+    return launch_pdl(k_row_forward_p2<T, LOGN, B>, grid, dim3(p2_threads<LOGN, B>()), smem, st, a);
+  }
+  if ((e = grant_smem(k_row_inverse_p2<T, LOGN, B>, smem, RowP2Grant<T, LOGN, B>::i)) != cudaSuccess)
+    return e;
+  return launch_pdl(k_row_inverse_p2<T, LOGN, B>, grid, dim3(p2_threads<LOGN, B>()), smem, st, a);
+}
+
+template <typename T, int LOGN>
+cudaError_t launch_row_p2_b(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
+                            cudaStream_t st) {
+  switch (a.QB) {
+    case 1: return launch_row_p2_inst<T, LOGN, 1>(forward, a, grid, smem, st);
+    case 2: return launch_row_p2_inst<T, LOGN, 2>(forward, a, grid, smem, st);
+    case 4: return launch_row_p2_inst<T, LOGN, 4>(forward, a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_row_p2(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
+                          cudaStream_t st) {
+  switch (p2_log2(a.pl.N)) {
+    case 8: return launch_row_p2_b<T, 8>(forward, a, grid, smem, st);
+    case 9: return launch_row_p2_b<T, 9>(forward, a, grid, smem, st);
+    case 10: return launch_row_p2_b<T, 10>(forward, a, grid, smem, st);
+    case 11: return launch_row_p2_b<T, 11>(forward, a, grid, smem, st);
+    case 12: return launch_row_p2_b<T, 12>(forward, a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, int blocks, int threads, size_t smem,
                               cudaStream_t st) {
@@ -1353,6 +1651,8 @@ extern template cudaError_t launch_row_pipe<float>(bool, const RowArgs<float>&, 
 extern template cudaError_t launch_row_pipe<double>(bool, const RowArgs<double>&, int, size_t, cudaStream_t);
 extern template cudaError_t row_pipe_blocks_per_sm<float>(bool, size_t, int*);
 extern template cudaError_t row_pipe_blocks_per_sm<double>(bool, size_t, int*);
+extern template cudaError_t launch_row_p2<float>(bool, const RowArgs<float>&, dim3, size_t, cudaStream_t);
+extern template cudaError_t launch_row_p2<double>(bool, const RowArgs<double>&, dim3, size_t, cudaStream_t);
 
 #endif
 

@@ -140,6 +140,9 @@ struct Plan {
   int rp, rp_nslot;
   size_t rp_smem_f, rp_smem_i;
   int rp_grid_f, rp_grid_i;
+  // power-of-two rows: compile-time Stockham kernels with the first stage fused into the load
+  int p2, QBi;             // QBi: class pairs per CTA of the inverse power-of-two pass
+  size_t p2_smem, p2_smem_i;
   int CB, NSEG, SL, col_threads, ncolblk;
   int row_threads, col_rows;   // target threads of a row-pass CTA; rows per column segment
   size_t col_smem;
@@ -178,7 +181,7 @@ static int check_tiling(const segsalsa_str_tiling* t, std::string& msg) {
   if (t->zfuse && t->zfuse != 1 && t->zfuse != 2 && t->zfuse != 4 && t->zfuse != 8 && t->zfuse != 16) {
     msg = "zfuse must be 0, 1, 2, 4, 8 or 16"; return SEGSALSA_ERR_ARG;
   }
-  if (t->row_pipe < 0 || t->row_pipe > 2) { msg = "row_pipe must be 0, 1 or 2"; return SEGSALSA_ERR_ARG; }
+  if (t->row_pipe < 0 || t->row_pipe > 3) { msg = "row_pipe must be 0, 1, 2 or 3"; return SEGSALSA_ERR_ARG; }
   return SEGSALSA_OK;
 }
 
@@ -282,7 +285,18 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   // while two CTAs still share an SM
   {
     const int req = tl ? tl->row_pipe : 0;
-    pl.rp = (req == 2 || (req == 0 && (long long)H * W >= ROWPIPE_DEFAULT_PIXELS)) ? 1 : 0;
+    // by default for rows of 2048 and more (measured faster there; shorter power-of-two rows
+    // run the one-unit kernels with more pairs per CTA at least as fast)
+    pl.p2 = (((req == 0 && W >= 2048) || req == 3) && p2_ok<T>(W, pl.blue, pl.QB, K)) ? 1 : 0;
+    // the inverse pass takes four pairs per CTA where the forward takes two (2048-point rows,
+    // K = 16: 271 -> 217 us at 2048 x 2048) unless the tiling fixes the pair count
+    pl.QBi = pl.QB;
+    if (pl.p2 && !(tl && tl->row_pairs) && pl.QB == 2 && p2_ok<T>(W, pl.blue, 4, K) && W >= 2048)
+      pl.QBi = 4;
+    pl.p2_smem = p2_smem_bytes<T>(W, pl.QB);
+    pl.p2_smem_i = p2_smem_bytes<T>(W, pl.QBi);
+    if (std::max(pl.p2_smem, pl.p2_smem_i) > 227 * 1024) pl.p2 = 0;
+    pl.rp = (req == 2 || (req == 0 && !pl.p2 && (long long)H * W >= ROWPIPE_DEFAULT_PIXELS)) ? 1 : 0;
     const size_t two = rowpipe_smem_bytes<T>(true, W, pl.Mf, pl.Wh, pl.QB, pl.ntx, pl.EWmax, 2, false);
     pl.rp_nslot = two <= 112 * 1024 ? 2 : 1;
     pl.rp_smem_f = std::max(
@@ -650,7 +664,14 @@ class Solver : public SolverBase {
       return SEGSALSA_OK;
     }
     const dim3 rg(pl.nqblk, pl.H);
-    if (pl.rp)
+    // the power-of-two kernels move a class block of a pixel as one vector: a caller's dense
+    // rhs or z must be aligned to it
+    const uintptr_t va = (uintptr_t)std::min<size_t>(16, 2 * pl.QB * sizeof(T)) - 1;
+    const bool p2 = pl.p2 && ((reinterpret_cast<uintptr_t>(src) & va) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(zout) & va) == 0);
+    if (p2)
+      SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row_p2<T>(true, ra, rg, pl.p2_smem, st); }));
+    else if (pl.rp)
       SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row_pipe<T>(true, ra, pl.rp_grid_f, pl.rp_smem_f, st); }));
     else
       SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
@@ -658,7 +679,16 @@ class Solver : public SolverBase {
     ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG; ca.SL = pl.SL;
     ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
     SGS_CUDA(launch(KIND_COL, [&]() { return launch_col<T>(ca, pl.ncolblk, pl.col_threads, pl.col_smem, st); }));
-    if (pl.rp)
+    if (p2) {
+      RowArgs<T> ri = ra;
+      ri.QB = pl.QBi;
+      ri.lgB = 0;
+      while ((1 << ri.lgB) < pl.QBi) ++ri.lgB;
+      ri.mgB = div_magic(pl.QBi);
+      const dim3 rgi((pl.K / 2 + pl.QBi - 1) / pl.QBi, pl.H);
+      SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row_p2<T>(false, ri, rgi, pl.p2_smem_i, st); }));
+    }
+    else if (pl.rp)
       SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row_pipe<T>(false, ra, pl.rp_grid_i, pl.rp_smem_i, st); }));
     else
       SGS_CUDA(launch(KIND_ROWI, [&]() { return launch_row<T>(false, ra, rg, pl.row, st); }));
@@ -1081,7 +1111,7 @@ class Solver : public SolverBase {
     t.tile_rows = pl.THmax; t.row_pairs = pl.QB; t.col_block = pl.CB;
     t.row_threads = pl.row_threads; t.col_rows = pl.col_rows;
     t.zfuse = pl.zf_cs ? pl.zf_cs : 1;
-    t.row_pipe = pl.rp ? 2 : 1;
+    t.row_pipe = pl.p2 ? 3 : pl.rp ? 2 : 1;
     return t;
   }
 
@@ -1754,7 +1784,7 @@ struct segsalsa_str_batch {
     const int cand_cols[] = {1, 2, 4, 8};
     const int cand_rthr[] = {128, 256, 512, 1024};
     const int cand_seg[] = {8, 16, 32};
-    const int cand_pipe[] = {1, 2};
+    const int cand_pipe[] = {1, 2, 3};
     for (auto& o : order) {
       const std::vector<int>& mem = groups[o.second];
       segsalsa_str_tiling cur = req[mem[0]];
@@ -1773,6 +1803,7 @@ struct segsalsa_str_batch {
           key.push_back(pl.THmax); key.push_back(pl.QB); key.push_back(pl.CB);
           key.push_back(pl.row.threads); key.push_back(pl.NSEG); key.push_back(pl.zf_cs);
           key.push_back(pl.rp);
+          key.push_back(pl.p2);
         }
         return true;
       };
@@ -1780,7 +1811,7 @@ struct segsalsa_str_batch {
       if (resolved(cur, key)) seen.insert(key);
       for (int f = 0; f < 6; ++f) {
         const int* cvs[6] = {cand_rows, cand_pairs, cand_cols, cand_rthr, cand_seg, cand_pipe};
-        const int ncs[6] = {7, 5, 4, 4, 3, 2};
+        const int ncs[6] = {7, 5, 4, 4, 3, 3};
         const int* cv = cvs[f];
         const int nc = ncs[f];
         segsalsa_str_tiling keep = cur;

@@ -28,6 +28,52 @@ def _pair(B, H, W, K, M, prec, row_pairs=0, lam=1.5):
 
 
 @pytest.mark.parametrize("H,W,K,M,prec,rp", [
+    (40, 256, 8, 1, "fp32", 0),     # 256-point rows, the default pair count
+    (37, 512, 16, 1, "fp32", 1),    # one pair per CTA: 8-byte loads and stores
+    (29, 1024, 16, 1, "fp32", 2),   # radix 8, 8, 8, 2
+    (45, 2048, 16, 1, "fp32", 2),   # radix 8, 8, 8, 4 (the 2048 x 2048 workload's rows)
+    (21, 2048, 8, 2, "fp32", 4),    # four pairs per CTA, 5x5 patch
+    (19, 4096, 4, 1, "fp32", 1),    # 4096-point rows
+    (23, 512, 8, 1, "fp64", 2),     # FP64: 16-byte pairs
+    (17, 1024, 4, 0, "fp64", 1),
+])
+def test_power_of_two_row_passes_match(B, H, W, K, M, prec, rp):
+    """Form 3 (compile-time plan, first stage fused into the load) against form 1: the
+    iterates of a traced solve are identical."""
+    sc = synth.scene(H, W, K, S=5, gap=2.0, noise_std=1.0, wrong_frac=0.05, seed=H + W + K + 7)
+    dt = np.float64 if prec == "fp64" else np.float32
+    p = sc.p.astype(dt)
+    mk = lambda pipe: B.Solver(B.make_params(H, W, K, M=M, sigma=0.5 + 0.5 * M, lam=1.5, mu=1.0,
+                                             precision=prec),
+                               tiling=B.make_tiling(row_pipe=pipe, row_pairs=rp))
+    s1, s3 = mk(1), mk(3)
+    assert s1.tiling()[6] == 1 and s3.tiling()[6] == 3
+    out = []
+    for s in (s1, s3):
+        s.set_probs(p)
+        tr = s.solve(12, trace_every=4)
+        out.append((s.get_z(), tr))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_power_of_two_linear_solve_against_oracle(B, prec):
+    H, W, K = 33, 1024, 8
+    dt = np.float64 if prec == "fp64" else np.float32
+    rhs = synth.random_field((K, H, W), seed=77).astype(dt)
+    s = B.Solver(B.make_params(H, W, K, M=1, sigma=0.5, precision=prec),
+                 tiling=B.make_tiling(row_pipe=3))
+    assert s.tiling()[6] == 3
+    z = hwk_to_khw(s.linear_solve(khw_to_hwk(rhs)))
+    s.close()
+    ref = O.linear_solve(rhs.astype(np.float64), O.gaussian_weights(1, 0.5), 1)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    assert max_abs(z, ref) <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("H,W,K,M,prec,rp", [
     (40, 37, 8, 1, "fp32", 0),      # direct prime row (37), small image
     (33, 127, 5, 1, "fp32", 0),     # Bluestein row, odd K (element-wise copies, zero fill)
     (29, 509, 4, 1, "fp32", 0),     # Bluestein row, vector copies
