@@ -1239,32 +1239,43 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const 
     const int t = it / B, q = it - t * B;
     const int cq = c0 + 2 * q;              // the pair's classes cq, cq + 1
     C v[8];
+    if (a.src) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int x = t + r * NB;
-      C c[1];
-      if (a.src) {
-        p2_load_block<T, 1>(a.src + ((size_t)y * N + x) * a.K + cq, c);
-      } else {
-        // p00 (+ p01) (+ p10) (+ p11), the order of gather_row16; absent covers not loaded
-        const int2 ox = __ldg(reinterpret_cast<const int2*>(a.offX) + x);
-        const bool hx = ox.y >= 0;
-        p2_load_block<T, 1>(a.P + rb0 + ox.x + cq, c);
-        C e[1];
-        if (hx) {
-          p2_load_block<T, 1>(a.P + rb0 + ox.y + cq, e);
-          c[0] = cadd(c[0], e[0]);
+      for (int r = 0; r < 8; ++r) {
+        C c[1];
+        p2_load_block<T, 1>(a.src + ((size_t)y * N + t + r * NB) * a.K + cq, c);
+        v[r] = c[0];
+      }
+    } else {
+      // p00 (+ p01) (+ p10) (+ p11), the order of gather_row16. All loads of the butterfly
+      // are issued before any sum (an absent cover aliases the first, its value is dropped),
+      // so that they are in flight together.
+      // (in two batches of four pixels, to keep the registers of three CTAs per SM)
+      const int rb1a = hy ? rb1 : rb0;
+#pragma unroll
+      for (int h = 0; h < 8; h += 4) {
+        C c00[4], c01[4], c10[4], c11[4];
+        bool hx[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int2 ox = __ldg(reinterpret_cast<const int2*>(a.offX) + t + (h + r) * NB);
+          hx[r] = ox.y >= 0;
+          const int o1 = hx[r] ? ox.y : ox.x;
+          C e[1];
+          p2_load_block<T, 1>(a.P + rb0 + ox.x + cq, e); c00[r] = e[0];
+          p2_load_block<T, 1>(a.P + rb0 + o1 + cq, e);   c01[r] = e[0];
+          p2_load_block<T, 1>(a.P + rb1a + ox.x + cq, e); c10[r] = e[0];
+          p2_load_block<T, 1>(a.P + rb1a + o1 + cq, e);  c11[r] = e[0];
         }
-        if (hy) {
-          p2_load_block<T, 1>(a.P + rb1 + ox.x + cq, e);
-          c[0] = cadd(c[0], e[0]);
-          if (hx) {
-            p2_load_block<T, 1>(a.P + rb1 + ox.y + cq, e);
-            c[0] = cadd(c[0], e[0]);
-          }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          C c = c00[r];
+          if (hx[r]) c = cadd(c, c01[r]);
+          if (hy) c = cadd(c, c10[r]);
+          if (hy && hx[r]) c = cadd(c, c11[r]);
+          v[h + r] = c;
         }
       }
-      v[r] = c[0];
     }
     p2_first<T, N, B>(v, t, q, Y);
   }
