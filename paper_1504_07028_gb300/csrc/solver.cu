@@ -233,8 +233,8 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.wide = M >= 3;
   pl.wntx1 = (W + 256 / pl.G - 1) / (256 / pl.G);
   pl.wntiles1 = pl.wntx1 * ((H + WG_TH - 1) / WG_TH);
-  // transpose: 256 / G pixels per block and round, at least four rounds, at most 8 blocks / SM
-  pl.wnblk2 = std::max(1, std::min(152 * 8, (pl.n + 4 * (256 / pl.G) - 1) / (4 * (256 / pl.G))));
+  // transpose: 256 / G pixels per block and round, at most 8 blocks per SM
+  pl.wnblk2 = std::max(1, std::min(152 * 8, (pl.n + 256 / pl.G - 1) / (256 / pl.G)));
   if (pl.wide) {
     if (wide_gram_smem<T>(M, pl.G) > 227 * 1024) {
       msg = "wide-patch tiles do not fit in shared memory"; return SEGSALSA_ERR_ARG;

@@ -26,7 +26,7 @@
 
 namespace sgs {
 
-constexpr int WG_TH = 4;   // rows of a gram tile (its columns: 256 / G)
+constexpr int WG_TH = 1;   // rows of a gram tile (its columns: 256 / G)
 
 template <typename T>
 struct WideArgs {
