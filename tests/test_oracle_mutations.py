@@ -74,7 +74,7 @@ def _sum_for_max(Jz, sp):                   # S_inf as the sum of the singular v
 
 
 MUTATIONS = [
-    ("shift", _wrong_shift, [P.test_jacobian_brute_force_loops]),
+    ("shift", _wrong_shift, [lambda: P.test_jacobian_brute_force_loops(1, 4, 5)]),
     ("prox_g1", _wrong_root, [P.test_prox_g1_stationarity]),
     ("prox_g2", _wrong_tau, [lambda: P.test_vtv_reduction_M0(1)]),
     ("prox_g2", _wrong_shrink, [lambda: P.test_prox_g2_moreau_characterisation(1)]),

@@ -32,8 +32,9 @@ def test_gaussian_weights_reading():
             assert w[j] == pytest.approx(w[sh.index((-dy, -dx))], abs=0)
 
 
-def test_jacobian_brute_force_loops():
-    K, H, W, M = 2, 4, 5, 1
+@pytest.mark.parametrize("M,H,W", [(1, 4, 5), (3, 8, 9), (5, 12, 13)])
+def test_jacobian_brute_force_loops(M, H, W):
+    K = 2
     z = _rand((K, H, W), 1)
     om = np.abs(_rand(((2 * M + 1) ** 2,), 2))
     J = O.jacobian(z, om, M)
@@ -50,9 +51,9 @@ def test_jacobian_brute_force_loops():
     assert np.allclose(Vm[i, 1 * K + 1], J[1, 1, :, 2, 3])
 
 
-@pytest.mark.parametrize("M", [0, 1, 2])
+@pytest.mark.parametrize("M", [0, 1, 2, 3, 5])
 def test_jacobian_adjoint(M):
-    K, H, W = 3, 7, 9
+    K, H, W = 3, 13, 12
     om = np.abs(_rand(((2 * M + 1) ** 2,), 3))
     x = _rand((K, H, W), 4)
     w = _rand(((2 * M + 1) ** 2, K, 2, H, W), 5)
@@ -61,10 +62,10 @@ def test_jacobian_adjoint(M):
     assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
 
 
-@pytest.mark.parametrize("M", [0, 1, 2])
+@pytest.mark.parametrize("M", [0, 1, 2, 3, 4, 5])
 def test_JTJ_equals_weighted_laplacian(M):
     """Periodic shifts are isometries: ||Jz||^2 = (sum omega^2)(||D_h z||^2 + ||D_v z||^2)."""
-    K, H, W = 2, 6, 8
+    K, H, W = 2, 12, 14
     om = np.abs(_rand(((2 * M + 1) ** 2,), 6))
     z = _rand((K, H, W), 7)
     c = np.sum(om ** 2)
