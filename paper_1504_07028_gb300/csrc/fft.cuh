@@ -1216,7 +1216,7 @@ __device__ __forceinline__ void p2_load_block(const T* __restrict__ src, cplx<T>
 // Threads of a power-of-two row CTA: one first-stage butterfly of one sequence each.
 template <int LOGN, int B>
 constexpr int p2_threads() {
-  return ((1 << LOGN) / 8 * B) > 512 ? 512 : ((1 << LOGN) / 8 * B);
+  return ((1 << LOGN) / 8 * B) > 1024 ? 1024 : ((1 << LOGN) / 8 * B);
 }
 
 template <typename T, int LOGN, int B>
@@ -1518,7 +1518,7 @@ cudaError_t launch_row_pipe(bool forward, const RowArgs<T>& a, int grid, size_t 
                             cudaStream_t st);
 template <typename T>
 cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks);
-// Power-of-two row passes (p2_ok): grid (class blocks, rows), N / 8 * QB threads (<= 512).
+// Power-of-two row passes (p2_ok): grid (class blocks, rows), N / 8 * QB threads (<= 1024).
 template <typename T>
 cudaError_t launch_row_p2(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
                           cudaStream_t st);

@@ -288,11 +288,21 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
     // by default for rows of 2048 and more (measured faster there; shorter power-of-two rows
     // run the one-unit kernels with more pairs per CTA at least as fast)
     pl.p2 = (((req == 0 && W >= 2048) || req == 3) && p2_ok<T>(W, pl.blue, pl.QB, K)) ? 1 : 0;
-    // the inverse pass takes four pairs per CTA where the forward takes two (2048-point rows,
-    // K = 16: 271 -> 217 us at 2048 x 2048) unless the tiling fixes the pair count
+    // pair count of the power-of-two kernels, unless the tiling fixes it: the largest of 4, 2, 1
+    // whose CTA (W / 8 x pairs threads, two transform buffers) fits (2048-point rows, K = 16:
+    // four pairs, forward 294 -> 256 us and inverse 216 -> 206 us at 2048 x 2048)
+    if (pl.p2 && !(tl && tl->row_pairs)) {
+      for (int qb : {4, 2, 1}) {
+        if (!p2_ok<T>(W, pl.blue, qb, K) || W / 8 * qb > 1024 ||
+            p2_smem_bytes<T>(W, qb) > 227 * 1024 || qb > Q)
+          continue;
+        pl.QB = qb;
+        break;
+      }
+      pl.nqblk = (Q + pl.QB - 1) / pl.QB;
+      pl.row = row_launch_config<T>(W, pl.Mf, pl.blue, pl.QB, pl.row_threads);
+    }
     pl.QBi = pl.QB;
-    if (pl.p2 && !(tl && tl->row_pairs) && pl.QB == 2 && p2_ok<T>(W, pl.blue, 4, K) && W >= 2048)
-      pl.QBi = 4;
     pl.p2_smem = p2_smem_bytes<T>(W, pl.QB);
     pl.p2_smem_i = p2_smem_bytes<T>(W, pl.QBi);
     if (std::max(pl.p2_smem, pl.p2_smem_i) > 227 * 1024) pl.p2 = 0;
