@@ -289,9 +289,16 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
  *   zfuse       : z-update (12) in one launch over a thread-block cluster of this many CTAs,
  *                 each owning a band of rows whose transforms and spectra stay in shared
  *                 memory (2, 4, 8 or 16); 1 = three launches (row transforms, column solves,
- *                 inverse row transforms); 0 = the library's choice (three launches: the
- *                 fused form measured slower on every shape tried). A fused request that the
- *                 band or the device cannot hold runs three launches (get_tiling reports 1).
+ *                 inverse row transforms); 3 = one launch of persistent CTAs that take the
+ *                 units of the three passes in order from a ticket counter (a column unit
+ *                 waits, bounded, until every row unit is done; an inverse unit until every
+ *                 column unit is; results bit-identical to three launches with the same
+ *                 tiling; column segments are lengthened where the column pass would need
+ *                 more than 512 threads; one-unit row form only; measured slower than the
+ *                 three launches chained by programmatic dependent launch: 145x145, K = 16,
+ *                 36.3 vs 30.8 us per iteration); 0 = the library's choice (three launches).
+ *                 A fused request that the band or the device cannot hold runs three
+ *                 launches (get_tiling reports 1).
  *   row_pipe    : form of the two row-transform passes: 1 = one CTA per (row, class block);
  *                 2 = persistent CTAs (one wave) that walk the (row, class block) units and
  *                 copy the next unit's input into shared memory asynchronously while the

@@ -508,16 +508,16 @@ __device__ __forceinline__ void store_pair(double2* dst, double2 a, double2 b) {
   dst[1] = b;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
+// One unit of the forward row pass: row y, class pairs q0 .. q0 + QB - 1, on the calling CTA
+// (any multiple of 32 threads; every loop strides by blockDim.x). OWN: the unit is the whole
+// kernel (programmatic-dependency wait before reading the rhs, trigger after the transform);
+// otherwise the caller has waited for the rhs already.
+template <typename T, bool OWN>
+__device__ __forceinline__ void row_forward_unit(const RowArgs<T>& a, int y, int q0,
+                                                 unsigned char* smem_raw) {
   using C = cplx<T>;
   constexpr int U = 8;  // independent element loads in flight per thread
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  // grid (class blocks, rows): the class blocks of one row run side by side, so the 32-byte
-  // sectors they share are read from DRAM once
-  const int y = blockIdx.y;
-  const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
   C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);  // second transform buffer
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
     cX = cs;
   }
   cp_async_commit();
-  pdl_wait();  // rhs / partials come from the previous kernel
+  if constexpr (OWN) pdl_wait();  // rhs / partials come from the previous kernel
   cp_async_wait_all();
   __syncthreads();
   T* Xf = reinterpret_cast<T*>(X);
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   }
   __syncthreads();
   const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
-  pdl_trigger();
+  if constexpr (OWN) pdl_trigger();
   // unpack the two real spectra of each pair: A = (X_k + conj X_{N-k})/2,
   // B = (X_k - conj X_{N-k})/(2i); one thread per pair, stored together when K is even
   for (int i = threadIdx.x; i < a.Wh * B; i += blockDim.x) {
@@ -621,6 +621,14 @@ __global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
   }
 }
 
+// grid (class blocks, rows): the class blocks of one row run side by side, so the 32-byte
+// sectors they share are read from DRAM once
+template <typename T>
+__global__ void __launch_bounds__(1024) k_row_forward(const RowArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  row_forward_unit<T, true>(a, blockIdx.y, blockIdx.x * a.QB, smem_raw);
+}
+
 // Dense rhs [n][K] from the sweep partials (checkpoint read-out).
 template <typename T>
 __global__ void k_gather_dense(const RowArgs<T> a) {
@@ -632,23 +640,21 @@ __global__ void k_gather_dense(const RowArgs<T> a) {
 }
 
 // ------------------------------------------------------------------- pass C (inverse rows)
-template <typename T>
-__global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
+// One unit of the inverse row pass (row y, class pairs q0 .. q0 + QB - 1); OWN as for
+// row_forward_unit.
+template <typename T, bool OWN>
+__device__ __forceinline__ void row_inverse_unit(const RowArgs<T>& a, int y, int q0,
+                                                 unsigned char* smem_raw) {
   using C = cplx<T>;
   constexpr int U = 8;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  // grid (class blocks, rows): the class blocks of one row run side by side, so the 32-byte
-  // sectors they share are read from DRAM once
-  const int y = blockIdx.y;
-  const int q0 = blockIdx.x * a.QB;
   const int B = a.QB;
   const int N = a.pl.N;
   C* Y = X + padded_elems<T>((size_t)a.pl.Mf * B);  // second transform buffer
   C* tab = Y + padded_elems<T>((size_t)a.pl.Mf * B);
   const FftTables<T> tb = row_tables<T>(a, tab);
   cp_async_commit();
-  pdl_wait();  // the spectrum comes from the column pass
+  if constexpr (OWN) pdl_wait();  // the spectrum comes from the column pass
   // load conj(A + iB) over the full frequency range (Hermitian extension), inverse DFT by
   // conj(DFT(conj(.)))/N
   const int tot = N * B;
@@ -687,7 +693,7 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
   cp_async_wait_all();
   __syncthreads();
   const C* R = dft_rows<T>(X, Y, B, a.mgB, a.pl, tb);
-  pdl_trigger();
+  if constexpr (OWN) pdl_trigger();
   const T inv = T(1) / T(N);
   constexpr int VE = 16 / sizeof(T);
   const bool vec = a.K % VE == 0 && (2 * B) % VE == 0 && 2 * (q0 + B) <= a.K &&
@@ -722,6 +728,12 @@ __global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
     const C v = dft_out<T>(R, B, x, qq, a.pl, tb);     // DFT(conj X)_x ; result = conj(v)/N
     a.z[((size_t)y * a.W + x) * a.K + k] = (part == 0) ? v.x * inv : -v.y * inv;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_row_inverse(const RowArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  row_inverse_unit<T, true>(a, blockIdx.y, blockIdx.x * a.QB, smem_raw);
 }
 
 // ------------------------------------------------ pipelined row passes (persistent CTAs)
@@ -1021,11 +1033,12 @@ struct ColArgs {
   cplx<T>* S;            // [H][C]
 };
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+// One unit of the column pass: complex columns blk * CB .. blk * CB + CB - 1 over all rows,
+// on a CTA of at least 2 CB NSEG threads; OWN as for row_forward_unit.
+template <typename T, bool OWN>
+__device__ __forceinline__ void col_solve_unit(const ColArgs<T>& a, int blk, unsigned char* smem_raw) {
   T* buf = reinterpret_cast<T*>(smem_raw);  // [H][2*CB]
-  const int c0 = blockIdx.x * a.CB;
+  const int c0 = blk * a.CB;
   const int nseq = 2 * a.CB;
   const int H = a.H;
   T* Sf = reinterpret_cast<T*>(a.S);
@@ -1033,7 +1046,7 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
   constexpr int V = 16 / sizeof(T);
   const bool vec = (2 * (size_t)a.C * sizeof(T)) % 16 == 0 && (nseq * sizeof(T)) % 16 == 0 &&
                    c0 + a.CB <= a.C;
-  pdl_wait();  // the spectrum comes from the row pass
+  if constexpr (OWN) pdl_wait();  // the spectrum comes from the row pass
   if (vec) {
     const int per_row = nseq / V;
     for (int i = threadIdx.x; i < H * per_row; i += blockDim.x) {
@@ -1094,7 +1107,7 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
       acc2 = beta * acc2 + buf[n * nseq + s];
       buf[n * nseq + s] = gain * acc2;
     }
-  pdl_trigger();
+  if constexpr (OWN) pdl_trigger();
   __syncthreads();
   if (vec) {
     const int per_row = nseq / V;
@@ -1108,6 +1121,117 @@ __global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
       const int y = i / nseq, ss = i % nseq;
       const int col2 = 2 * c0 + ss;
       if (col2 < 2 * a.C) Sf[(size_t)y * 2 * a.C + col2] = buf[i];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_col_solve(const ColArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  col_solve_unit<T, true>(a, blockIdx.x, smem_raw);
+}
+
+// ---------------------------------------- the three passes in one launch (ordered tickets)
+//
+// The z-update as one launch of persistent CTAs. The work units of the three passes are
+// numbered in pass order (forward (row, class block) units in row-major order, then the column
+// blocks, then the inverse units) and handed out by an atomic ticket counter. A column unit
+// starts once every forward unit has signalled completion, an inverse unit once every column
+// unit has. A unit only ever waits for units with smaller tickets, and those were taken by
+// CTAs that were already running and wait only for smaller tickets themselves, so the launch
+// completes for any grid size and any number of co-resident CTAs: no cooperative launch is
+// needed. The units run the bodies of k_row_forward / k_col_solve / k_row_inverse, so the
+// results are bit-identical to the three launches. Each dependency wait is bounded (error
+// flag, then the CTA stops taking tickets); the last CTA to finish returns the counters to 0
+// for the next launch.
+template <typename T>
+struct ZseqArgs {
+  RowArgs<T> f, i;       // forward and inverse row passes (their QB may differ)
+  ColArgs<T> c;
+  int nqf, nqi;          // class blocks per row of the forward / inverse pass
+  int nf, nc, ni;        // units of each pass
+  unsigned int* ctr;     // [4]: ticket, forward units done, column units done, CTAs done
+  int* err;
+  long long budget;      // clock cycles of one dependency wait
+  int probe;             // 1: the column units wait for one forward unit more than exists
+};
+
+// Relaxed GPU-scope read of a counter (polling; an acquire fence follows the last read, so the
+// polls themselves do not order, or invalidate, anything).
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;\n" ::: "memory"); }
+
+constexpr int ZSEQ_MAX_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(ZSEQ_MAX_THREADS) k_zupdate_seq(const ZseqArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_ticket;
+  pdl_wait();  // the rhs (partials or dense) comes from the previous kernel
+  const int nfc = a.nf + a.nc, total = nfc + a.ni;
+  bool triggered = false;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = (int)atomicAdd(a.ctr, 1u);
+      if (t >= a.nf && t < total) {
+        const unsigned int* dep = t < nfc ? a.ctr + 1 : a.ctr + 2;
+        const unsigned int need = t < nfc ? (unsigned)(a.nf + a.probe) : (unsigned)a.nc;
+        if (ld_relaxed_u32(dep) < need) {
+          const long long t0 = clock64();
+          while (ld_relaxed_u32(dep) < need) {
+            if (clock64() - t0 > a.budget) {
+              atomicExch(a.err, 1);
+              t = -1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+        fence_acq_rel_gpu();  // acquire: the producers' writes are visible to this CTA
+      }
+      s_ticket = t;
+    }
+    __syncthreads();
+    const int t = s_ticket;
+    if (t < 0 || t >= total) break;
+    if (t < a.nf) {
+      const int y = t / a.nqf, qb = t - y * a.nqf;
+      row_forward_unit<T, false>(a.f, y, qb * a.f.QB, smem_raw);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.ctr + 1, 1u);
+      }
+    } else if (t < nfc) {
+      col_solve_unit<T, false>(a.c, t - a.nf, smem_raw);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.ctr + 2, 1u);
+      }
+    } else {
+      if (!triggered) {
+        pdl_trigger();  // the next kernel may start its prologue once every CTA is here
+        triggered = true;
+      }
+      const int u = t - nfc;
+      const int y = u / a.nqi, qb = u - y * a.nqi;
+      row_inverse_unit<T, false>(a.i, y, qb * a.i.QB, smem_raw);
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.ctr + 3, 1u) == gridDim.x - 1) {
+      // every CTA has taken its last ticket: nothing reads the counters any more
+      atomicExch(a.ctr, 0u);
+      atomicExch(a.ctr + 1, 0u);
+      atomicExch(a.ctr + 2, 0u);
+      atomicExch(a.ctr + 3, 0u);
     }
   }
 }
@@ -1518,6 +1642,11 @@ cudaError_t launch_row_pipe(bool forward, const RowArgs<T>& a, int grid, size_t 
                             cudaStream_t st);
 template <typename T>
 cudaError_t row_pipe_blocks_per_sm(bool forward, size_t smem, int* blocks);
+// The three passes in one launch (k_zupdate_seq) on `grid` CTAs; `grid` <= 0 only grants the
+// shared memory and returns in *blocks the number of CTAs one SM holds.
+template <typename T>
+cudaError_t launch_zseq(const ZseqArgs<T>& a, int grid, int threads, size_t smem, cudaStream_t st,
+                        int* blocks = nullptr);
 // Power-of-two row passes (p2_ok): grid (class blocks, rows), N / 8 * QB threads (<= 1024).
 template <typename T>
 cudaError_t launch_row_p2(bool forward, const RowArgs<T>& a, dim3 grid, size_t smem,
@@ -1563,6 +1692,24 @@ cudaError_t launch_row(bool forward, const RowArgs<T>& a, dim3 grid, const RowLa
     return cudaGetLastError();
   }
   return launch_pdl(k_row_inverse<T>, grid, dim3(rl.threads), rl.smem, st, a);
+}
+
+template <typename T>
+struct ZseqGrant {
+  static SmemGrants g;
+};
+template <typename T> SmemGrants ZseqGrant<T>::g;
+
+template <typename T>
+cudaError_t launch_zseq(const ZseqArgs<T>& a, int grid, int threads, size_t smem, cudaStream_t st,
+                        int* blocks) {
+  cudaError_t e = grant_smem(k_zupdate_seq<T>, smem, ZseqGrant<T>::g);
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) {
+    *blocks = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_zupdate_seq<T>, threads, smem);
+  }
+  return launch_pdl(k_zupdate_seq<T>, dim3(grid), dim3(threads), smem, st, a);
 }
 
 template <typename T>

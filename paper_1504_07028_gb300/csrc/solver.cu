@@ -149,6 +149,10 @@ struct Plan {
   // z-update fused over a cluster (0: three passes), its class-pair groups, threads, memory
   int zf_cs, zf_qg, zf_rmax, zf_groups, zf_threads;
   size_t zf_smem;
+  // z-update as one launch of persistent CTAs taking the units of the three passes in order
+  // (ordered tickets; the one-unit row form only)
+  int zs, zs_threads, zs_grid;
+  size_t zs_smem;
   int nproj_blk, nprior_blk;
   // wide patches (M >= 3): two-launch sweep (gram + transpose tiles) writing a dense rhs
   int wide, wntx1, wntiles1, wnblk2;
@@ -178,8 +182,9 @@ static int check_tiling(const segsalsa_str_tiling* t, std::string& msg) {
   if (t->col_block < 0 || t->col_block > 8) { msg = "col_block must be 0..8"; return SEGSALSA_ERR_ARG; }
   if (t->row_threads && (t->row_threads < 64 || t->row_threads > 1024)) { msg = "row_threads must be 0 or 64..1024"; return SEGSALSA_ERR_ARG; }
   if (t->col_rows && (t->col_rows < 2 || t->col_rows > 4096)) { msg = "col_rows must be 0 or 2..4096"; return SEGSALSA_ERR_ARG; }
-  if (t->zfuse && t->zfuse != 1 && t->zfuse != 2 && t->zfuse != 4 && t->zfuse != 8 && t->zfuse != 16) {
-    msg = "zfuse must be 0, 1, 2, 4, 8 or 16"; return SEGSALSA_ERR_ARG;
+  if (t->zfuse && t->zfuse != 1 && t->zfuse != 2 && t->zfuse != 3 && t->zfuse != 4 && t->zfuse != 8 &&
+      t->zfuse != 16) {
+    msg = "zfuse must be 0, 1, 2, 3, 4, 8 or 16"; return SEGSALSA_ERR_ARG;
   }
   if (t->row_pipe < 0 || t->row_pipe > 3) { msg = "row_pipe must be 0, 1, 2 or 3"; return SEGSALSA_ERR_ARG; }
   return SEGSALSA_OK;
@@ -336,6 +341,17 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.NSEG = std::max(1, std::min(H / pl.col_rows, 1024 / nseq));
   col_segments(H, pl.NSEG, nseq, (int)sizeof(T), pl.SL, pl.NSEG);
   pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
+  // the one-launch z-update runs the column units on its CTAs of at most ZSEQ_MAX_THREADS:
+  // longer segments where the column pass would need more (a three-launch handle given the
+  // reported col_rows plans the same segments)
+  if (tl && tl->zfuse == 3 && !pl.p2 && !pl.rp) {
+    while (pl.col_threads > ZSEQ_MAX_THREADS && pl.col_rows < H) {
+      ++pl.col_rows;
+      pl.NSEG = std::max(1, std::min(H / pl.col_rows, 1024 / nseq));
+      col_segments(H, pl.NSEG, nseq, (int)sizeof(T), pl.SL, pl.NSEG);
+      pl.col_threads = (nseq * pl.NSEG + 31) / 32 * 32;
+    }
+  }
   pl.ncolblk = (pl.Wh * K + pl.CB - 1) / pl.CB;
   // z-update in one launch, on request only (measured slower than the three passes at every
   // shape tried): clusters of CS CTAs (one band of rows each) per class pair, when a band's
@@ -346,7 +362,7 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   {
     const int req = tl ? tl->zfuse : 0;
     std::vector<int> cands;
-    if (req > 1) cands = {req};
+    if (req > 1 && req != 3) cands = {req};
     const bool direct = !pl.blue && largest_prime_factor(pl.Mf) > 7;
     for (int cs : cands) {
       const int rmax = (H + cs - 1) / cs;
@@ -362,6 +378,19 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
       pl.zf_threads = std::max(128, std::min(512, t));
       pl.zf_smem = sm;
       break;
+    }
+  }
+  // the three passes in one launch of persistent CTAs (one-unit row form only; grid set at
+  // create from the device's occupancy)
+  pl.zs = pl.zs_threads = pl.zs_grid = 0;
+  pl.zs_smem = 0;
+  {
+    const int req = tl ? tl->zfuse : 0;
+    if (req == 3 && !pl.p2 && !pl.rp && !pl.zf_cs && pl.col_threads <= ZSEQ_MAX_THREADS) {
+      pl.zs = 1;
+      pl.zs_threads = std::min(ZSEQ_MAX_THREADS, (std::max(pl.row.threads, pl.col_threads) + 31) / 32 * 32);
+      pl.zs_smem = std::max(pl.row.smem, pl.col_smem);
+      if (pl.zs_smem > 227 * 1024) pl.zs = 0;
     }
   }
   // diagnostics
@@ -397,6 +426,7 @@ struct Buffers {
   double *dsq, *dproj, *dprior, *dtrace;
   int* flag;
   int* err;  // set by kernels whose bounded waits gave up
+  unsigned int* zctr;  // [4] work-ticket counters of the one-launch z-update (0 between launches)
   T* omega;
   int *covY, *covX, *offX;
   T *beta, *gain, *wfac;
@@ -428,6 +458,7 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.dtrace = c.take<double>(6 * (size_t)TRACE_CAP);
   b.flag = c.take<int>(1);
   b.err = c.take<int>(1);
+  b.zctr = c.take<unsigned int>(4);
   b.omega = c.take<T>(pl.L);
   b.covY = c.take<int>((size_t)pl.H * MAXCOV);
   b.covX = c.take<int>((size_t)pl.W * MAXCOV);
@@ -527,6 +558,16 @@ class Solver : public SolverBase {
     else SGS_CUDA(prepare_sweep<T>(pl.M, pl.G, pl.sweep_smem, pl.sweep_smem_diag));
     SGS_CUDA(prepare_fft<T>(pl.row, pl.col_smem));
     if (pl.zf_cs && zfused_max_clusters<T>(pl.zf_cs, pl.zf_threads, pl.zf_smem) < 1) pl.zf_cs = 0;
+    if (pl.zs) {
+      int dev = 0, nsm = 0, nb = 0;
+      SGS_CUDA(cudaGetDevice(&dev));
+      SGS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      ZseqArgs<T> none{};
+      SGS_CUDA(launch_zseq<T>(none, 0, pl.zs_threads, pl.zs_smem, st, &nb));
+      const long long most = std::max<long long>(std::max<long long>((long long)pl.nqblk * pl.H, pl.ncolblk), 1);
+      pl.zs_grid = (int)std::min<long long>(most, (long long)nb * nsm);
+      if (nb < 1) pl.zs = 0;
+    }
     if (pl.rp) {
       // one wave of persistent CTAs; three launches of the one-unit kernels if none fits
       int dev = 0, nsm = 0, nbf = 0, nbi = 0;
@@ -548,6 +589,7 @@ class Solver : public SolverBase {
     for (int j = 0; j < pl.L; ++j) om[j] = (T)omega[j];
     SGS_CUDA(cudaMemcpyAsync(b.omega, om.data(), sizeof(T) * pl.L, cudaMemcpyHostToDevice, st));
     SGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), st));
+    SGS_CUDA(cudaMemsetAsync(b.zctr, 0, 4 * sizeof(unsigned int), st));
     SGS_CUDA(cudaMemcpyAsync(b.covY, pl.covY.data(), sizeof(int) * pl.covY.size(), cudaMemcpyHostToDevice, st));
     SGS_CUDA(cudaMemcpyAsync(b.covX, pl.covX.data(), sizeof(int) * pl.covX.size(), cudaMemcpyHostToDevice, st));
     {
@@ -673,6 +715,21 @@ class Solver : public SolverBase {
       SGS_CUDA(launch(KIND_ZF, [&]() { return launch_zfused<T>(za, pl.zf_groups, pl.zf_threads, pl.zf_smem, st); }));
       return SEGSALSA_OK;
     }
+    ColArgs<T> ca{};
+    ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG; ca.SL = pl.SL;
+    ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
+    if (pl.zs) {
+      ZseqArgs<T> za{};
+      za.f = ra; za.i = ra; za.c = ca;
+      za.nqf = za.nqi = pl.nqblk;
+      za.nf = za.ni = pl.nqblk * pl.H;
+      za.nc = pl.ncolblk;
+      za.ctr = b.zctr; za.err = b.err;
+      za.budget = wait_budget;
+      za.probe = wait_probe ? 1 : 0;
+      SGS_CUDA(launch(KIND_ZF, [&]() { return launch_zseq<T>(za, pl.zs_grid, pl.zs_threads, pl.zs_smem, st); }));
+      return SEGSALSA_OK;
+    }
     const dim3 rg(pl.nqblk, pl.H);
     // the power-of-two kernels move a class block of a pixel as one vector: a caller's dense
     // rhs or z must be aligned to it
@@ -685,9 +742,6 @@ class Solver : public SolverBase {
       SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row_pipe<T>(true, ra, pl.rp_grid_f, pl.rp_smem_f, st); }));
     else
       SGS_CUDA(launch(KIND_ROWF, [&]() { return launch_row<T>(true, ra, rg, pl.row, st); }));
-    ColArgs<T> ca{};
-    ca.H = pl.H; ca.C = pl.Wh * pl.K; ca.K = pl.K; ca.CB = pl.CB; ca.NSEG = pl.NSEG; ca.SL = pl.SL;
-    ca.beta = b.beta; ca.gain = b.gain; ca.wfac = b.wfac; ca.nwarm = b.nwarm; ca.S = b.S;
     SGS_CUDA(launch(KIND_COL, [&]() { return launch_col<T>(ca, pl.ncolblk, pl.col_threads, pl.col_smem, st); }));
     if (p2) {
       RowArgs<T> ri = ra;
@@ -971,6 +1025,7 @@ class Solver : public SolverBase {
     SGS_CUDA(cudaStreamSynchronize(st));
     if (errflag) {
       cudaMemsetAsync(b.err, 0, sizeof(int), st);
+      cudaMemsetAsync(b.zctr, 0, 4 * sizeof(unsigned int), st);
       return fail(SEGSALSA_ERR_TIMEOUT, "a device-side wait gave up (bounded wait exceeded)");
     }
     if (trace) {
@@ -1084,6 +1139,16 @@ class Solver : public SolverBase {
     T* out = dev ? reinterpret_cast<T*>(z) : b.zp;
     if ((rc = z_update(src, out))) return rc;
     if (!dev && (rc = copy_out(z, b.zp, nK, 0))) return rc;
+    if (pl.zs) {  // the one-launch form waits between its passes (bounded)
+      int errflag = 0;
+      SGS_CUDA(cudaMemcpyAsync(&errflag, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SGS_CUDA(cudaStreamSynchronize(st));
+      if (errflag) {
+        cudaMemsetAsync(b.err, 0, sizeof(int), st);
+        cudaMemsetAsync(b.zctr, 0, 4 * sizeof(unsigned int), st);
+        return fail(SEGSALSA_ERR_TIMEOUT, "a device-side wait gave up (bounded wait exceeded)");
+      }
+    }
     SGS_CUDA(cudaStreamSynchronize(st));
     return SEGSALSA_OK;
   }
@@ -1120,7 +1185,7 @@ class Solver : public SolverBase {
     segsalsa_str_tiling t;
     t.tile_rows = pl.THmax; t.row_pairs = pl.QB; t.col_block = pl.CB;
     t.row_threads = pl.row_threads; t.col_rows = pl.col_rows;
-    t.zfuse = pl.zf_cs ? pl.zf_cs : 1;
+    t.zfuse = pl.zs ? 3 : pl.zf_cs ? pl.zf_cs : 1;
     t.row_pipe = pl.p2 ? 3 : pl.rp ? 2 : 1;
     return t;
   }
@@ -1147,8 +1212,12 @@ class Solver : public SolverBase {
   }
   void advance(int len) override {
     iter += len;
-    nlaunch[KIND_ROWF] += len; nlaunch[KIND_COL] += len; nlaunch[KIND_ROWI] += len;
-    nlaunch[KIND_SWEEP] += len;
+    if (pl.zs || pl.zf_cs) {
+      nlaunch[KIND_ZF] += len;
+    } else {
+      nlaunch[KIND_ROWF] += len; nlaunch[KIND_COL] += len; nlaunch[KIND_ROWI] += len;
+    }
+    nlaunch[KIND_SWEEP] += pl.wide ? 2 * len : len;
   }
   int enqueue_eager_iteration(cudaStream_t s) override {
     cudaStream_t keep = st;
@@ -1166,6 +1235,7 @@ class Solver : public SolverBase {
   }
   int clear_err(cudaStream_t s) override {
     SGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), s));
+    SGS_CUDA(cudaMemsetAsync(b.zctr, 0, 4 * sizeof(unsigned int), s));
     return SEGSALSA_OK;
   }
   void invalidate() override { have_probs = false; iter = 0; rhs_dense = false; }

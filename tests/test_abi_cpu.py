@@ -89,7 +89,7 @@ def test_tiling_struct_matches_header():
     ((33, 0, 0), False), ((8, -1, 0), False), ((8, 0, 9), False), ((8, 65, 0), False),
     ((0, 0, 0, 256, 16), True), ((0, 0, 0, 32, 0), False), ((0, 0, 0, 2048, 0), False),
     ((0, 0, 0, 0, 1), False), ((0, 0, 0, 0, 0, 1), True), ((0, 0, 0, 0, 0, 16), True),
-    ((0, 0, 0, 0, 0, 3), False), ((0, 0, 0, 0, 0, 32), False), ((0, 0, 0, 0, 0, -1), False),
+    ((0, 0, 0, 0, 0, 3), True), ((0, 0, 0, 0, 0, 5), False), ((0, 0, 0, 0, 0, 32), False), ((0, 0, 0, 0, 0, -1), False),
     ((0, 0, 0, 0, 0, 0, 1), True), ((0, 0, 0, 0, 0, 0, 2), True), ((0, 0, 0, 0, 0, 0, 3), True),
     ((0, 0, 0, 0, 0, 0, 4), False), ((0, 0, 0, 0, 0, 0, -1), False)])
 def test_tiling_checks(lib, tiling, ok):
