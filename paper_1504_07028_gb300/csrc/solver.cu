@@ -238,8 +238,8 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   pl.wide = M >= 3;
   pl.wntx1 = (W + 256 / pl.G - 1) / (256 / pl.G);
   pl.wntiles1 = pl.wntx1 * ((H + WG_TH - 1) / WG_TH);
-  // transpose: 256 / G pixels per block and round, at most 8 blocks per SM
-  pl.wnblk2 = std::max(1, std::min(152 * 8, (pl.n + 256 / pl.G - 1) / (256 / pl.G)));
+  // transpose: the gram tiles again (one row of 256 / G targets), at most 8 blocks per SM
+  pl.wnblk2 = std::max(1, std::min(152 * 8, pl.wntiles1));
   if (pl.wide) {
     if (wide_gram_smem<T>(M, pl.G) > 227 * 1024) {
       msg = "wide-patch tiles do not fit in shared memory"; return SEGSALSA_ERR_ARG;
@@ -420,7 +420,8 @@ struct Carver {
 template <typename T>
 struct Buffers {
   T *p, *z, *dloc, *d2, *P, *P2, *zp, *tmp, *rhsd;
-  T* wbuf;  // wide patches: omega_j (u2 + d2) of the last sweep, [n][L][K][2]
+  T* wbuf;  // wide patches: scratch [n][L][K][2] (the old d2 of a traced sweep; checkpoint read-out)
+  T* coef;  // wide patches: [n][4] the 2 x 2 prox matrix A of the last sweep (d2 = V (A - I))
   cplx<T>* S;
   int32_t* lab;
   double *dsq, *dproj, *dprior, *dtrace;
@@ -451,6 +452,7 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.rhsd = c.take<T>(nK);
   b.S = c.take<cplx<T>>((size_t)pl.H * pl.Wh * pl.K);
   b.wbuf = pl.wide ? c.take<T>(2 * (size_t)pl.L * nK) : nullptr;
+  b.coef = pl.wide ? c.take<T>(4 * (size_t)pl.n) : nullptr;
   b.lab = c.take<int32_t>(pl.n);
   b.dsq = c.take<double>(std::max(pl.ntiles, pl.wntiles1));
   b.dproj = c.take<double>(4 * (size_t)pl.nproj_blk);
@@ -763,7 +765,8 @@ class Solver : public SolverBase {
     if (pl.wide) {
       WideArgs<T> w{};
       w.H = pl.H; w.W = pl.W; w.K = pl.K; w.M = pl.M; w.L = pl.L;
-      w.z = b.z; w.p = b.p; w.dloc = b.dloc; w.d2 = b.d2; w.wbuf = b.wbuf; w.rhs = b.rhsd;
+      w.z = b.z; w.p = b.p; w.dloc = b.dloc; w.V = b.d2; w.coef = b.coef; w.scratch = b.wbuf;
+      w.rhs = b.rhsd;
       w.gtd = b.P2; w.diag_sq = b.dsq; w.omega = b.omega;
       w.tau = (T)(lambda / mu); w.mu = (T)mu; w.invK = (T)(1.0 / pl.K); w.sp = sp;
       w.ntx1 = pl.wntx1; w.ntiles1 = pl.wntiles1; w.nblk2 = pl.wnblk2;
@@ -842,6 +845,7 @@ class Solver : public SolverBase {
     SGS_LAUNCH(KIND_OTHER, (k_init_z<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.p, b.z, n, K)));
     SGS_CUDA(cudaMemsetAsync(b.dloc, 0, sizeof(T) * 3 * nK, st));
     SGS_CUDA(cudaMemsetAsync(b.d2, 0, sizeof(T) * 2 * pl.L * nK, st));
+    if (pl.wide) SGS_CUDA(cudaMemsetAsync(b.coef, 0, sizeof(T) * 4 * (size_t)n, st));  // V = 0: d2 = 0
     SGS_CUDA(cudaStreamSynchronize(st));
     iter = 0;
     rhs_dense = false;
@@ -1077,7 +1081,14 @@ class Solver : public SolverBase {
     const size_t nK = (size_t)pl.n * pl.K;
     int rc;
     if (z && (rc = copy_out(z, b.z, nK, dev))) return rc;
-    if (d2 && (rc = copy_out(d2, b.d2, 2 * pl.L * nK, dev))) return rc;
+    if (d2 && pl.wide) {
+      // the wide sweep stores d2 as (V, A): d2 = V (A - I)
+      T* dst = dev ? reinterpret_cast<T*>(d2) : b.wbuf;
+      SGS_CUDA(launch_wide_dual<T>(b.d2, b.coef, dst, pl.n, pl.L * pl.K, st));
+      if (!dev && (rc = copy_out(d2, b.wbuf, 2 * pl.L * nK, 0))) return rc;
+    } else if (d2 && (rc = copy_out(d2, b.d2, 2 * pl.L * nK, dev))) {
+      return rc;
+    }
     void* dl[3] = {d1, d3, d4};
     for (int j = 0; j < 3; ++j) {
       if (!dl[j]) continue;
@@ -1110,6 +1121,7 @@ class Solver : public SolverBase {
     int rc;
     if ((rc = copy_in(b.z, z, nK, dev))) return rc;
     if ((rc = copy_in(b.d2, d2, 2 * pl.L * nK, dev))) return rc;
+    if (pl.wide) SGS_CUDA(launch_wide_coef_identity<T>(b.coef, pl.n, st));  // V = d2, A = 2I
     const void* dl[3] = {d1, d3, d4};
     for (int j = 0; j < 3; ++j) {
       if ((rc = copy_in(b.tmp, dl[j], nK, dev))) return rc;

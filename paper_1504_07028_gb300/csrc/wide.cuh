@@ -1,24 +1,31 @@
 // SALSA sweep (eqs. 12-14) for wide patches, (2M+1) x (2M+1) with M = 3, 4, 5 (the 7x7 to 11x11
 // patches of Sec. 5's patch-size study). The fused sweep keeps a pixel's 2L Jacobian entries
 // per class and its J^T scatter window in registers, which does not fit for L up to 121; here
-// the same update is split into two launches that never hold more than one shift per thread:
+// the same update is split into two launches that never hold more than one shift per thread.
 //
-//   k_wide_gram (one pixel per G lanes, class k on lane k, tiles of WG_TH rows):
-//     pass 1 over the shifts: v2 = J z - d2, the Gram matrix [[a, b], [b, c]] = V^T V of
-//     eq. (5) by a G-lane sum, and the Schatten-p prox coefficients u2 = V [[A11, A12],
-//     [A12, A22]] (the closed form the fused sweep uses); pass 2 over the shifts: u2, the dual
-//     update d2 <- u2 - v2 (in place: each entry is read and written by one thread) and
-//     w = u2 + d2, stored for the transpose; then the pixel-local MPOs of g1, g3, g4 with their
+// Stored form of the prior's dual. The MPO of g2 maps the pixel's block v (2L rows of K) to
+// u = v A with the symmetric 2 x 2 matrix A of the Schatten-p closed form, and the dual becomes
+// d2' = u - v = v (A - I). The wide sweep therefore stores V = v (the last prox argument, in the
+// d2 buffer, [n][L][K][2]) and A per pixel ([n][4]: A11, A12, A22, unused) instead of d2 itself:
+// d2 = V (A - I) entry by entry. (A = 2I stores d2 = V; V = 0 stores d2 = 0 for any A.)
+//
+//   k_wide_gram (one pixel per G lanes, class k on lane k, tiles of WG_TH rows): one pass over
+//     the shifts reads V and the pixel's A, forms the dual d2 = V (A - I) and the new argument
+//     v = omega_j grad z(m + s_j) - d2 (eq. 13's J z - d2), stores v over V in place (each entry
+//     is read and written by one thread) and sums the Gram matrix [[a, b], [b, c]] = v^T v of
+//     eq. (5) by a G-lane sum; then the new A, and the pixel-local MPOs of g1, g3, g4 with their
 //     duals and their part (u1 + d1) + (u3 + d3) + (u4 + d4) of the rhs.
 //
 //   k_wide_jt (one target pixel per G lanes): every target pixel m adds, shift by shift,
-//       omega_j [w_h(m - s_j - e_h) - w_h(m - s_j) - w_v(m - s_j) + w_v(m - s_j - e_v)]
-//     (J^T of eq. 12 as a gather, in a fixed order: deterministic); the w of neighbouring
-//     targets overlap, so the repeated reads are served by L1. The result rhs = local part +
-//     J^T w is dense; the z-update reads it directly.
+//       w_h(m - s_j - e_h) - w_h(m - s_j) - w_v(m - s_j) + w_v(m - s_j - e_v)
+//     with w = omega_j (u + d2') = omega_j (v A + (v A - v)) recomputed from the stored v and A
+//     of each source pixel (J^T of eq. 12 as a gather, in a fixed order: deterministic). Nothing
+//     is written but the rhs, so the neighbouring targets' reads of the same entries do not
+//     race; they are served by L1 / L2. The result rhs = local part + J^T w is dense; the
+//     z-update reads it directly.
 //
-// Traced variants also accumulate ||d^{k+1} - d^k||^2 per tile and write G^T d^{k+1}
-// densely (dual residual).
+// Traced variants also accumulate ||d^{k+1} - d^k||^2 per tile (the gram kernel keeps the old
+// dual in a scratch buffer for a second pass) and write G^T d^{k+1} densely (dual residual).
 #pragma once
 
 #include "common.cuh"
@@ -34,8 +41,9 @@ struct WideArgs {
   const T* z;        // [n][K]
   const T* p;        // [n][K]
   T* dloc;           // [n][3][K]  (d1, d3, d4)
-  T* d2;             // [n][L][K][2]
-  T* wbuf;           // [n][L][K][2]: omega_j (u2 + d2) of the last sweep
+  T* V;              // [n][L][K][2]: the prior's last prox argument v (d2 = V (A - I))
+  T* coef;           // [n][4]: A11, A12, A22 of that prox
+  T* scratch;        // DIAG: [n][L][K][2] the old dual d2 of the traced sweep
   T* rhs;            // [n][K] dense rhs (local part from the gram kernel, completed by k_wide_jt)
   T* gtd;            // DIAG: [n][K] dense G^T d^{k+1}
   double* diag_sq;   // DIAG: per-tile sums of squared dual changes
@@ -51,6 +59,22 @@ __host__ __device__ inline size_t wide_gram_smem(int M, int G) {
   const int NC = 256 / G;
   return sizeof(T) * (size_t)(WG_TH + 2 * M + 1) * (NC + 2 * M + 1) * G;
 }
+
+// A of pixel `pix` (two 2-vectors: (A11, A12), (A22, unused)).
+template <typename T>
+__device__ __forceinline__ void load_coef(const T* coef, size_t pix, T& a11, T& a12, T& a22) {
+  using V2 = typename Vec2Of<T>::type;
+  const V2* c = reinterpret_cast<const V2*>(coef) + 2 * pix;
+  const V2 c0 = c[0], c1 = c[1];
+  a11 = c0.x; a12 = c0.y; a22 = c1.x;
+}
+
+// The two components of u = v A in one fixed evaluation order (explicit fma), so that every
+// kernel that forms u or the dual u - v from the stored (V, A) gets the same bits.
+template <typename T>
+__device__ __forceinline__ T prox_h(T vx, T vy, T a11, T a12) { return fma(vy, a12, vx * a11); }
+template <typename T>
+__device__ __forceinline__ T prox_v(T vx, T vy, T a12, T a22) { return fma(vy, a22, vx * a12); }
 
 template <typename T, int G, bool DIAG, bool SIMP>
 __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
@@ -87,22 +111,39 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
     const size_t pix = (size_t)y * a.W + (colok ? x : 0);
     const T* zc = zs + ((r + M) * EW + (c + M)) * G + g;     // z at this pixel, class g
     using V2 = typename Vec2Of<T>::type;
-    V2* d2p = reinterpret_cast<V2*>(a.d2) + pix * L * K + g;   // shift j at + j K
-    V2* wp = reinterpret_cast<V2*>(a.wbuf) + pix * L * K + g;
-    // pass 1: Gram matrix over the (j, k) rows of the pixel
+    V2* vp = reinterpret_cast<V2*>(a.V) + pix * L * K + g;   // shift j at + j K
+    V2* ep = reinterpret_cast<V2*>(a.scratch) + pix * L * K + g;
+    T o11 = T(0), o12 = T(0), o22 = T(0);
+    if (colok) load_coef(a.coef, pix, o11, o12, o22);
+    // the dual of the last sweep, the new argument v (stored over V) and the Gram matrix
     T ga = T(0), gb = T(0), gc = T(0);
     if (kok) {
-#pragma unroll 8
-      for (int j = 0; j < L; ++j) {
+      constexpr int UB = 8;   // shifts whose V loads are issued together
+      for (int j0 = 0; j0 < L; j0 += UB) {
+        V2 vb[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u)
+          if (j0 + u < L) vb[u] = vp[(size_t)(j0 + u) * K];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = j0 + u;
+        if (j >= L) break;
         const int jy = j / P;
         const T* zq = zc + ((jy - M) * EW + (j - jy * P - M)) * G;
         const T w = a.omega[j];
-        const V2 dd = d2p[(size_t)j * K];
-        const T vh = w * (zq[G] - zq[0]) - dd.x;
-        const T vv = w * (zq[EW * G] - zq[0]) - dd.y;
-        ga += vh * vh;
-        gb += vh * vv;
-        gc += vv * vv;
+        const V2 vo = vb[u];
+        V2 dd;
+        dd.x = prox_h(vo.x, vo.y, o11, o12) - vo.x;
+        dd.y = prox_v(vo.x, vo.y, o12, o22) - vo.y;
+        V2 v;
+        v.x = w * (zq[G] - zq[0]) - dd.x;
+        v.y = w * (zq[EW * G] - zq[0]) - dd.y;
+        vp[(size_t)j * K] = v;
+        if constexpr (DIAG) ep[(size_t)j * K] = dd;
+        ga += v.x * v.x;
+        gb += v.x * v.y;
+        gc += v.y * v.y;
+      }
       }
     }
     ga = group_sum<G>(ga);
@@ -110,25 +151,23 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
     gc = group_sum<G>(gc);
     T A11, A12, A22;
     schatten_coeffs<T>(ga, gb, gc, tau, a.sp, A11, A12, A22);
-    // pass 2: u2 = V A, d2 <- u2 - v2, w = omega_j (u2 + d2)
-    if (kok) {
-#pragma unroll 8
-      for (int j = 0; j < L; ++j) {
-        const int jy = j / P;
-        const T* zq = zc + ((jy - M) * EW + (j - jy * P - M)) * G;
-        const T w = a.omega[j];
-        const V2 od = d2p[(size_t)j * K];
-        const T vh = w * (zq[G] - zq[0]) - od.x;
-        const T vv = w * (zq[EW * G] - zq[0]) - od.y;
-        const T uh = vh * A11 + vv * A12;
-        const T uv = vh * A12 + vv * A22;
-        V2 nd, wd;
-        nd.x = uh - vh; nd.y = uv - vv;
-        wd.x = w * (uh + nd.x); wd.y = w * (uv + nd.y);
-        d2p[(size_t)j * K] = nd;
-        wp[(size_t)j * K] = wd;
-        if constexpr (DIAG)
-          sq += (nd.x - od.x) * (nd.x - od.x) + (nd.y - od.y) * (nd.y - od.y);
+    if (colok && g == 0) {
+      using V2c = typename Vec2Of<T>::type;
+      V2c* cp = reinterpret_cast<V2c*>(a.coef) + 2 * pix;
+      V2c c0, c1;
+      c0.x = A11; c0.y = A12; c1.x = A22; c1.y = T(0);
+      cp[0] = c0;
+      cp[1] = c1;
+    }
+    if constexpr (DIAG) {
+      // ||d2' - d2||^2 with d2' = v (A - I): v and the old dual read back (this thread's writes)
+      if (kok) {
+        for (int j = 0; j < L; ++j) {
+          const V2 v = vp[(size_t)j * K], od = ep[(size_t)j * K];
+          const T nx = prox_h(v.x, v.y, A11, A12) - v.x;
+          const T ny = prox_v(v.x, v.y, A12, A22) - v.y;
+          sq += (nx - od.x) * (nx - od.x) + (ny - od.y) * (ny - od.y);
+        }
       }
     }
     // pixel-local MPOs of g1, g3, g4 and their duals (as the fused sweep)
@@ -184,50 +223,137 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
   }
 }
 
+// Shared memory of k_wide_jt: the A of a tile's source window ((2M + 2) rows x (NC + 2M + 1)
+// columns, four values each), and per shift its V offset for interior targets, (dy, dx) and
+// omega_j.
+template <typename T>
+__host__ __device__ inline size_t wide_jt_smem(int M, int G) {
+  const int NC = 256 / G, L = (2 * M + 1) * (2 * M + 1);
+  const size_t win = (size_t)(2 * M + 2) * (NC + 2 * M + 1) * 4 * sizeof(T);
+  return win + (size_t)L * (sizeof(long long) + 2 * sizeof(int) + sizeof(T));
+}
+
 template <typename T, int G, bool DIAG>
 __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
   using V2 = typename Vec2Of<T>::type;
-  constexpr int PPB = 256 / G;
+  constexpr int NC = 256 / G;
+  constexpr int UJ = 4;   // shifts whose V loads are issued together
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int K = a.K, M = a.M, P = 2 * M + 1, L = a.L;
-  const int g = threadIdx.x % G;
-  const V2* wv2 = reinterpret_cast<const V2*>(a.wbuf);
-  const V2* dv2 = reinterpret_cast<const V2*>(a.d2);
-  const int n = a.H * a.W;
-  pdl_wait();  // w, d2 and the local rhs come from k_wide_gram
-  for (int m0 = blockIdx.x * PPB; m0 < n; m0 += gridDim.x * PPB) {
-    const int m = m0 + threadIdx.x / G;
-    if (m >= n || g >= K) continue;   // no block-wide operations below
-    const int my = m / a.W, mx = m - my * a.W;
+  const int EWc = NC + 2 * M + 1, EHc = 2 * M + 2;
+  T* cw = reinterpret_cast<T*>(smem_raw);                                   // [EHc][EWc][4]
+  long long* offv = reinterpret_cast<long long*>(cw + (size_t)EHc * EWc * 4);  // [L]
+  int* dyx = reinterpret_cast<int*>(offv + L);                                // [L][2]
+  T* om = reinterpret_cast<T*>(dyx + 2 * L);                                  // [L]
+  const int g = threadIdx.x % G, c = threadIdx.x / G;
+  const V2* vv2 = reinterpret_cast<const V2*>(a.V);
+  const long long LK = (long long)L * K;
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    const int jy = j / P, dy = jy - M, dx = j - jy * P - M;
+    dyx[2 * j] = dy;
+    dyx[2 * j + 1] = dx;
+    offv[j] = (-(long long)dy * a.W - dx) * LK + (long long)j * K;   // V2 units, m - s_j
+    om[j] = a.omega[j];
+  }
+  pdl_wait();  // v, A and the local rhs come from k_wide_gram
+  for (int tile = blockIdx.x; tile < a.ntiles1; tile += gridDim.x) {
+    const int y = tile / a.ntx1, x0 = (tile % a.ntx1) * NC;
+    __syncthreads();  // the previous tile's window is no longer read
+    // A of the sources m - s_j - {0, e_h, e_v} of the tile's targets (periodic)
+    for (int idx = threadIdx.x; idx < EHc * EWc; idx += blockDim.x) {
+      const int ry = idx / EWc, rx = idx - ry * EWc;
+      const int py = wrap_idx(y - M - 1 + ry, a.H), px = wrap_idx(x0 - M - 1 + rx, a.W);
+      T a11, a12, a22;
+      load_coef(a.coef, (size_t)py * a.W + px, a11, a12, a22);
+      cw[4 * idx] = a11;
+      cw[4 * idx + 1] = a12;
+      cw[4 * idx + 2] = a22;
+    }
+    __syncthreads();
+    const int x = x0 + c;
+    if (x >= a.W || g >= K) continue;   // no block-wide operation before the next tile's
+    const long long m = (long long)y * a.W + x;
+    const bool inner = y >= M + 1 && y <= a.H - 1 - M && x >= M + 1 && x <= a.W - 1 - M;
     T acc = T(0), accd = T(0);
-#pragma unroll 4
-    for (int j = 0; j < L; ++j) {
-      const int jy = j / P;
-      const int dy = jy - M, dx = j - jy * P - M;
-      // i0 = m - s_j, ih = i0 - e_h, iv = i0 - e_v (periodic; |s_j| <= M < H, W)
-      int y0 = my - dy, x0 = mx - dx;
-      y0 += (y0 < 0) ? a.H : 0;
-      y0 -= (y0 >= a.H) ? a.H : 0;
-      x0 += (x0 < 0) ? a.W : 0;
-      x0 -= (x0 >= a.W) ? a.W : 0;
-      const int xh = x0 == 0 ? a.W - 1 : x0 - 1, yv = y0 == 0 ? a.H - 1 : y0 - 1;
-      const size_t o0 = (((size_t)y0 * a.W + x0) * L + j) * K + g;
-      const size_t oh = (((size_t)y0 * a.W + xh) * L + j) * K + g;
-      const size_t ov = (((size_t)yv * a.W + x0) * L + j) * K + g;
-      const V2 w0 = wv2[o0];
-      const T wh = a.wbuf[2 * oh], wv = a.wbuf[2 * ov + 1];
-      acc += wh - w0.x - w0.y + wv;
-      if constexpr (DIAG) {
-        const T om = a.omega[j];
-        const V2 d0 = dv2[o0];
-        const T dh = a.d2[2 * oh], dv = a.d2[2 * ov + 1];
-        accd += om * dh - om * d0.x - om * d0.y + om * dv;
+    for (int j0 = 0; j0 < L; j0 += UJ) {
+      V2 v0[UJ], vh[UJ], vv[UJ];
+#pragma unroll
+      for (int u = 0; u < UJ; ++u) {
+        const int j = j0 + u;
+        if (j >= L) break;
+        long long o0, oh, ov;
+        if (inner) {
+          o0 = m * LK + offv[j] + g;
+          oh = o0 - LK;
+          ov = o0 - (long long)a.W * LK;
+        } else {
+          // i0 = m - s_j, ih = i0 - e_h, iv = i0 - e_v (periodic; |s_j| <= M < H, W)
+          int ys = y - dyx[2 * j], xs = x - dyx[2 * j + 1];
+          ys += (ys < 0) ? a.H : 0;
+          ys -= (ys >= a.H) ? a.H : 0;
+          xs += (xs < 0) ? a.W : 0;
+          xs -= (xs >= a.W) ? a.W : 0;
+          const int xh = xs == 0 ? a.W - 1 : xs - 1, yv = ys == 0 ? a.H - 1 : ys - 1;
+          o0 = (((long long)ys * a.W + xs) * L + j) * K + g;
+          oh = (((long long)ys * a.W + xh) * L + j) * K + g;
+          ov = (((long long)yv * a.W + xs) * L + j) * K + g;
+        }
+        v0[u] = vv2[o0];
+        vh[u] = vv2[oh];
+        vv[u] = vv2[ov];
+      }
+#pragma unroll
+      for (int u = 0; u < UJ; ++u) {
+        const int j = j0 + u;
+        if (j >= L) break;
+        // window position of i0 (the window starts at (y - M - 1, x0 - M - 1))
+        const int w0 = (M + 1 - dyx[2 * j]) * EWc + (c + M + 1 - dyx[2 * j + 1]);
+        const T* c0 = cw + 4 * w0;
+        const T* ch = c0 - 4;
+        const T* cv = c0 - 4 * EWc;
+        const T u0x = prox_h(v0[u].x, v0[u].y, c0[0], c0[1]);
+        const T u0y = prox_v(v0[u].x, v0[u].y, c0[1], c0[2]);
+        const T n0x = u0x - v0[u].x, n0y = u0y - v0[u].y;
+        const T uhx = prox_h(vh[u].x, vh[u].y, ch[0], ch[1]);
+        const T nhx = uhx - vh[u].x;
+        const T uvy = prox_v(vv[u].x, vv[u].y, cv[1], cv[2]);
+        const T nvy = uvy - vv[u].y;
+        const T o = om[j];
+        acc += o * (uhx + nhx) - o * (u0x + n0x) - o * (u0y + n0y) + o * (uvy + nvy);
+        if constexpr (DIAG) accd += o * nhx - o * n0x - o * n0y + o * nvy;
       }
     }
-    const size_t o = (size_t)m * K + g;
-    a.rhs[o] += acc;
-    if constexpr (DIAG) a.gtd[o] += accd;
+    const size_t oo = (size_t)m * K + g;
+    a.rhs[oo] += acc;
+    if constexpr (DIAG) a.gtd[oo] += accd;
   }
   pdl_trigger();
+}
+
+// d2 = V (A - I) written out densely ([n][L][K][2]; checkpoint read-out).
+template <typename T>
+__global__ void k_wide_dual(const T* __restrict__ V, const T* __restrict__ coef, T* __restrict__ d2,
+                            int n, int LK) {
+  const size_t tot = (size_t)n * LK;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    T a11, a12, a22;
+    load_coef(coef, i / LK, a11, a12, a22);
+    const T vx = V[2 * i], vy = V[2 * i + 1];
+    d2[2 * i] = prox_h(vx, vy, a11, a12) - vx;
+    d2[2 * i + 1] = prox_v(vx, vy, a12, a22) - vy;
+  }
+}
+
+// A = 2 I for every pixel, so that V holds d2 itself (checkpoint load).
+template <typename T>
+__global__ void k_wide_coef_identity(T* coef, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    coef[4 * (size_t)i] = T(2);
+    coef[4 * (size_t)i + 1] = T(0);
+    coef[4 * (size_t)i + 2] = T(2);
+    coef[4 * (size_t)i + 3] = T(0);
+  }
 }
 
 // Launch both kernels of one wide-patch sweep (defined in wide.cu for float and double).
@@ -235,5 +361,10 @@ template <typename T>
 cudaError_t launch_wide(const WideArgs<T>& a, int G, bool diag, bool simplex, cudaStream_t st);
 template <typename T>
 cudaError_t prepare_wide(int M, int G);
+// Dense d2 from the stored form (V, A), and the stored form of a given d2 (A = 2I).
+template <typename T>
+cudaError_t launch_wide_dual(const T* V, const T* coef, T* d2, int n, int LK, cudaStream_t st);
+template <typename T>
+cudaError_t launch_wide_coef_identity(T* coef, int n, cudaStream_t st);
 
 }  // namespace sgs

@@ -1,4 +1,6 @@
 // FLOAT instantiations of the wide-patch sweep (k_wide_gram, k_wide_jt) and their launchers.
+#include <algorithm>
+
 #include "wide.cuh"
 
 namespace sgs {
@@ -7,15 +9,20 @@ template <int G, bool DIAG, bool SIMP>
 struct WideGramGrant { static SmemGrants g; };
 template <int G, bool DIAG, bool SIMP> SmemGrants WideGramGrant<G, DIAG, SIMP>::g;
 
+template <int G, bool DIAG>
+struct WideJtGrant { static SmemGrants g; };
+template <int G, bool DIAG> SmemGrants WideJtGrant<G, DIAG>::g;
+
 template <int G, bool DIAG, bool SIMP>
 static cudaError_t wide_g(const WideArgs<float>& a, cudaStream_t st) {
-  const size_t s1 = wide_gram_smem<float>(a.M, G);
+  const size_t s1 = wide_gram_smem<float>(a.M, G), s2 = wide_jt_smem<float>(a.M, G);
   cudaError_t e = grant_smem(k_wide_gram<float, G, DIAG, SIMP>, s1, WideGramGrant<G, DIAG, SIMP>::g);
   if (e != cudaSuccess) return e;
+  if ((e = grant_smem(k_wide_jt<float, G, DIAG>, s2, WideJtGrant<G, DIAG>::g)) != cudaSuccess) return e;
   if (st == reinterpret_cast<cudaStream_t>(-1)) return cudaSuccess;  // grants only
   if ((e = launch_pdl(k_wide_gram<float, G, DIAG, SIMP>, dim3(a.ntiles1), dim3(256), s1, st, a)) != cudaSuccess)
     return e;
-  return launch_pdl(k_wide_jt<float, G, DIAG>, dim3(a.nblk2), dim3(256), 0, st, a);
+  return launch_pdl(k_wide_jt<float, G, DIAG>, dim3(a.nblk2), dim3(256), s2, st, a);
 }
 
 template <int G>
@@ -44,6 +51,21 @@ cudaError_t prepare_wide<float>(int M, int G) {
     for (int s = 0; s < 2; ++s)
       if (cudaError_t e = launch_wide<float>(a, G, d, s, none)) return e;
   return cudaSuccess;
+}
+
+template <>
+cudaError_t launch_wide_dual<float>(const float* V, const float* coef, float* d2, int n, int LK, cudaStream_t st) {
+  const size_t tot = (size_t)n * LK;
+  const int blocks = (int)std::min<size_t>((tot + 255) / 256, 152 * 16);
+  k_wide_dual<float><<<blocks, 256, 0, st>>>(V, coef, d2, n, LK);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_wide_coef_identity<float>(float* coef, int n, cudaStream_t st) {
+  const int blocks = std::min((n + 255) / 256, 152 * 16);
+  k_wide_coef_identity<float><<<blocks, 256, 0, st>>>(coef, n);
+  return cudaGetLastError();
 }
 
 }  // namespace sgs

@@ -1,4 +1,6 @@
 // DOUBLE instantiations of the wide-patch sweep (k_wide_gram, k_wide_jt) and their launchers.
+#include <algorithm>
+
 #include "wide.cuh"
 
 namespace sgs {
@@ -7,15 +9,20 @@ template <int G, bool DIAG, bool SIMP>
 struct WideGramGrant { static SmemGrants g; };
 template <int G, bool DIAG, bool SIMP> SmemGrants WideGramGrant<G, DIAG, SIMP>::g;
 
+template <int G, bool DIAG>
+struct WideJtGrant { static SmemGrants g; };
+template <int G, bool DIAG> SmemGrants WideJtGrant<G, DIAG>::g;
+
 template <int G, bool DIAG, bool SIMP>
 static cudaError_t wide_g(const WideArgs<double>& a, cudaStream_t st) {
-  const size_t s1 = wide_gram_smem<double>(a.M, G);
+  const size_t s1 = wide_gram_smem<double>(a.M, G), s2 = wide_jt_smem<double>(a.M, G);
   cudaError_t e = grant_smem(k_wide_gram<double, G, DIAG, SIMP>, s1, WideGramGrant<G, DIAG, SIMP>::g);
   if (e != cudaSuccess) return e;
+  if ((e = grant_smem(k_wide_jt<double, G, DIAG>, s2, WideJtGrant<G, DIAG>::g)) != cudaSuccess) return e;
   if (st == reinterpret_cast<cudaStream_t>(-1)) return cudaSuccess;  // grants only
   if ((e = launch_pdl(k_wide_gram<double, G, DIAG, SIMP>, dim3(a.ntiles1), dim3(256), s1, st, a)) != cudaSuccess)
     return e;
-  return launch_pdl(k_wide_jt<double, G, DIAG>, dim3(a.nblk2), dim3(256), 0, st, a);
+  return launch_pdl(k_wide_jt<double, G, DIAG>, dim3(a.nblk2), dim3(256), s2, st, a);
 }
 
 template <int G>
@@ -44,6 +51,21 @@ cudaError_t prepare_wide<double>(int M, int G) {
     for (int s = 0; s < 2; ++s)
       if (cudaError_t e = launch_wide<double>(a, G, d, s, none)) return e;
   return cudaSuccess;
+}
+
+template <>
+cudaError_t launch_wide_dual<double>(const double* V, const double* coef, double* d2, int n, int LK, cudaStream_t st) {
+  const size_t tot = (size_t)n * LK;
+  const int blocks = (int)std::min<size_t>((tot + 255) / 256, 152 * 16);
+  k_wide_dual<double><<<blocks, 256, 0, st>>>(V, coef, d2, n, LK);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_wide_coef_identity<double>(double* coef, int n, cudaStream_t st) {
+  const int blocks = std::min((n + 255) / 256, 152 * 16);
+  k_wide_coef_identity<double><<<blocks, 256, 0, st>>>(coef, n);
+  return cudaGetLastError();
 }
 
 }  // namespace sgs

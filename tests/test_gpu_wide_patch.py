@@ -112,6 +112,30 @@ def test_wide_checkpoint_resume(B):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_wide_state_round_trip_is_exact(B, prec):
+    """The wide sweep keeps the prior's dual as (V, A) with d2 = V (A - I). get_state writes d2
+    out, set_state loads it back as V = d2, A = 2I; a handle resumed from the checkpoint must
+    continue bit for bit like the original (traced iterations included)."""
+    H, W, K, M, sigma = 26, 23, 5, 3, 1.5
+    sc = synth.scene(H, W, K, S=4, gap=2.0, noise_std=1.0, wrong_frac=0.0, seed=133)
+    dt = np.float64 if prec == "fp64" else np.float32
+    a = _solver(B, H, W, K, M, sigma, 1.5, 1.0, 2, prec)
+    a.set_probs(sc.p.astype(dt))
+    a.solve(7, trace_every=3)
+    st = a.get_state()
+    b = _solver(B, H, W, K, M, sigma, 1.5, 1.0, 2, prec)
+    b.set_probs(sc.p.astype(dt))
+    b.set_state(st, a.get_iteration())
+    ta = a.solve(9, trace_every=3)
+    tb = b.solve(9, trace_every=3)
+    assert np.array_equal(a.get_z(), b.get_z())
+    assert np.array_equal(a.get_state()["d2"], b.get_state()["d2"])
+    assert np.array_equal(np.asarray(ta)[:, 1:], np.asarray(tb)[:, 1:])
+    a.close()
+    b.close()
+
+
 def test_wide_and_narrow_patches_in_one_batch(B):
     cases = [(24, 30, 4, 1), (28, 21, 5, 3), (22, 25, 4, 5)]
     scenes = [synth.scene(H, W, K, S=4, gap=2.0, noise_std=1.0, wrong_frac=0.0, seed=140 + j)
