@@ -56,8 +56,10 @@ struct WideArgs {
 
 template <typename T>
 __host__ __device__ inline size_t wide_gram_smem(int M, int G) {
-  const int NC = 256 / G;
-  return sizeof(T) * (size_t)(WG_TH + 2 * M + 1) * (NC + 2 * M + 1) * G;
+  const int NC = 256 / G, L = (2 * M + 1) * (2 * M + 1);
+  // the z tile with its halo, then per shift its z-tile offset and omega_j
+  return sizeof(T) * (size_t)(WG_TH + 2 * M + 1) * (NC + 2 * M + 1) * G +
+         (size_t)L * (sizeof(int) + sizeof(T));
 }
 
 // A of pixel `pix` (two 2-vectors: (A11, A12), (A22, unused)).
@@ -85,6 +87,13 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
   const int M = a.M, K = a.K, L = a.L;
   const int P = 2 * M + 1;
   const int EW = NC + 2 * M + 1, EH = WG_TH + 2 * M + 1;
+  T* om = zs + (size_t)EH * EW * G;                   // [L] omega_j
+  int* zoff = reinterpret_cast<int*>(om + L);         // [L] z-tile offset of shift j
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    const int jy = j / P;
+    zoff[j] = ((jy - M) * EW + (j - jy * P - M)) * G;
+    om[j] = a.omega[j];
+  }
   const int tile = blockIdx.x;
   const int y0 = (tile / a.ntx1) * WG_TH, x0 = (tile % a.ntx1) * NC;
   const int g = threadIdx.x % G, c = threadIdx.x / G;
@@ -128,9 +137,8 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
       for (int u = 0; u < UB; ++u) {
         const int j = j0 + u;
         if (j >= L) break;
-        const int jy = j / P;
-        const T* zq = zc + ((jy - M) * EW + (j - jy * P - M)) * G;
-        const T w = a.omega[j];
+        const T* zq = zc + zoff[j];
+        const T w = om[j];
         const V2 vo = vb[u];
         V2 dd;
         dd.x = prox_h(vo.x, vo.y, o11, o12) - vo.x;
@@ -224,14 +232,31 @@ __global__ void __launch_bounds__(256) k_wide_gram(const WideArgs<T> a) {
 }
 
 // Shared memory of k_wide_jt: the A of a tile's source window ((2M + 2) rows x (NC + 2M + 1)
-// columns, four values each), and per shift its V offset for interior targets, (dy, dx) and
-// omega_j.
+// columns, four values each), then per shift its V offset for interior targets (8 bytes),
+// omega_j, (dy, dx) and its window entry (4-byte values last: L is odd).
 template <typename T>
 __host__ __device__ inline size_t wide_jt_smem(int M, int G) {
   const int NC = 256 / G, L = (2 * M + 1) * (2 * M + 1);
   const size_t win = (size_t)(2 * M + 2) * (NC + 2 * M + 1) * 4 * sizeof(T);
-  return win + (size_t)L * (sizeof(long long) + 2 * sizeof(int) + sizeof(T));
+  return win + (size_t)L * (sizeof(long long) + 3 * sizeof(int) + sizeof(T));
 }
+
+// The four stored values of one window entry (A11, A12, A22, unused) in one shared load.
+template <typename T> struct Coef4;
+template <> struct Coef4<float> {
+  float a11, a12, a22, pad;
+  __device__ static Coef4 at(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+  }
+};
+template <> struct Coef4<double> {
+  double a11, a12, a22, pad;
+  __device__ static Coef4 at(const double* p) {
+    const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+    return {v.x, v.y, w.x, w.y};
+  }
+};
 
 template <typename T, int G, bool DIAG>
 __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
@@ -243,8 +268,9 @@ __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
   const int EWc = NC + 2 * M + 1, EHc = 2 * M + 2;
   T* cw = reinterpret_cast<T*>(smem_raw);                                   // [EHc][EWc][4]
   long long* offv = reinterpret_cast<long long*>(cw + (size_t)EHc * EWc * 4);  // [L]
-  int* dyx = reinterpret_cast<int*>(offv + L);                                // [L][2]
-  T* om = reinterpret_cast<T*>(dyx + 2 * L);                                  // [L]
+  T* om = reinterpret_cast<T*>(offv + L);                                     // [L]
+  int* dyx = reinterpret_cast<int*>(om + L);                                  // [L][2]
+  int* woff = dyx + 2 * L;                                                    // [L]
   const int g = threadIdx.x % G, c = threadIdx.x / G;
   const V2* vv2 = reinterpret_cast<const V2*>(a.V);
   const long long LK = (long long)L * K;
@@ -253,6 +279,7 @@ __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
     dyx[2 * j] = dy;
     dyx[2 * j + 1] = dx;
     offv[j] = (-(long long)dy * a.W - dx) * LK + (long long)j * K;   // V2 units, m - s_j
+    woff[j] = 4 * ((M + 1 - dy) * EWc + (M + 1 - dx));   // window entry of i0 (column 0)
     om[j] = a.omega[j];
   }
   pdl_wait();  // v, A and the local rhs come from k_wide_gram
@@ -306,17 +333,16 @@ __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
       for (int u = 0; u < UJ; ++u) {
         const int j = j0 + u;
         if (j >= L) break;
-        // window position of i0 (the window starts at (y - M - 1, x0 - M - 1))
-        const int w0 = (M + 1 - dyx[2 * j]) * EWc + (c + M + 1 - dyx[2 * j + 1]);
-        const T* c0 = cw + 4 * w0;
-        const T* ch = c0 - 4;
-        const T* cv = c0 - 4 * EWc;
-        const T u0x = prox_h(v0[u].x, v0[u].y, c0[0], c0[1]);
-        const T u0y = prox_v(v0[u].x, v0[u].y, c0[1], c0[2]);
+        // window entry of i0 (the window starts at (y - M - 1, x0 - M - 1))
+        const T* p0 = cw + woff[j] + 4 * c;
+        const Coef4<T> c0 = Coef4<T>::at(p0), ch = Coef4<T>::at(p0 - 4),
+                       cv = Coef4<T>::at(p0 - 4 * EWc);
+        const T u0x = prox_h(v0[u].x, v0[u].y, c0.a11, c0.a12);
+        const T u0y = prox_v(v0[u].x, v0[u].y, c0.a12, c0.a22);
         const T n0x = u0x - v0[u].x, n0y = u0y - v0[u].y;
-        const T uhx = prox_h(vh[u].x, vh[u].y, ch[0], ch[1]);
+        const T uhx = prox_h(vh[u].x, vh[u].y, ch.a11, ch.a12);
         const T nhx = uhx - vh[u].x;
-        const T uvy = prox_v(vv[u].x, vv[u].y, cv[1], cv[2]);
+        const T uvy = prox_v(vv[u].x, vv[u].y, cv.a12, cv.a22);
         const T nvy = uvy - vv[u].y;
         const T o = om[j];
         acc += o * (uhx + nhx) - o * (u0x + n0x) - o * (u0y + n0y) + o * (uvy + nvy);
