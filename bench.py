@@ -152,7 +152,10 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name):
+def make_workload(name, patch=None):
+    """Scene, solver settings and description of a workload; `patch` (M) replaces the 3x3
+    patch of the HxW workloads by a (2M+1)x(2M+1) one (Gaussian sigma = max(0.5, M/2))."""
+    import dataclasses
     from paper_1504_07028_gb300 import synth
     if name == "145x145":
         sc = synth.scene_145x145_k16()
@@ -181,6 +184,12 @@ def make_workload(name):
         desc = f"{H}x{W} K=16, 3x3 Gaussian patch sigma=0.5, lambda=2, mu=1, 200 iterations, p=1"
     else:
         raise SystemExit(f"unknown workload {name}")
+    if patch is not None:
+        if "x" not in name or name in ("145x145", "64x64"):
+            raise SystemExit("--patch applies to the HxW workloads only")
+        cfgs = [dataclasses.replace(c, M=patch, sigma=max(0.5, 0.5 * patch)) for c in cfgs]
+        desc = desc.replace("3x3 Gaussian patch sigma=0.5",
+                            f"{2 * patch + 1}x{2 * patch + 1} Gaussian patch sigma={max(0.5, 0.5 * patch)}")
     return sc, cfgs, desc
 
 
@@ -334,7 +343,7 @@ def run_reference(args, rank, world):
     if args.workload == "diff256":
         run_reference_diff(args)
         return
-    sc, cfgs, desc = make_workload(args.workload)
+    sc, cfgs, desc = make_workload(args.workload, args.patch)
     per_p = max(1, args.ref_iters)
     for _ in range(min(args.warmup, 1)):
         oracle_sample(sc, cfgs, 1)
@@ -370,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     Bu.build()
-    sc, cfgs, desc = make_workload(args.workload)
+    sc, cfgs, desc = make_workload(args.workload, args.patch)
     K, H, W = sc.K, sc.H, sc.W
     n = H * W
     # the solves of a step are independent: each gets its own handle, stream and host thread,
@@ -473,7 +482,7 @@ def run_ours(args, rank, world, local_rank):
             stats[kname] = (c0 + cnt, m0 + ms)
         sb, ib = s.traffic_model()
         c_sw, m_sw = st["sweep"]
-        n_sw = args.steps * cfg.iters          # sweeps (a wide-patch sweep is two launches)
+        n_sw = args.steps * cfg.iters          # sweeps (a wide-patch sweep is three launches)
         sw_bytes_tot += sb * n_sw
         per_solve.append({
             "M": cfg.M, "L": (2 * cfg.M + 1) ** 2, "schatten_p": str(cfg.schatten_p),
@@ -1147,6 +1156,8 @@ def main():
                     help="2048x2048 (default), 145x145, 64x64, HxW (K=16 synthetic scene), patchsweep, or "
                          "batch64 (64 uneven images in one batch), mlr610x340 (MLR front end), or diff256 "
                          "(differentiable solver)")
+    ap.add_argument("--patch", type=int, default=None,
+                    help="HxW workloads: patch radius M (default 1, the 3x3 patch)")
     ap.add_argument("--no-autotune", action="store_true", help="batch64: default tilings")
     ap.add_argument("--tune-iters", type=int, default=4, help="batch64: iterations per trial")
     ap.add_argument("--cpu-iters", type=int, default=4)

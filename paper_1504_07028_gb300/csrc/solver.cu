@@ -770,8 +770,8 @@ class Solver : public SolverBase {
       w.gtd = b.P2; w.diag_sq = b.dsq; w.omega = b.omega;
       w.tau = (T)(lambda / mu); w.mu = (T)mu; w.invK = (T)(1.0 / pl.K); w.sp = sp;
       w.ntx1 = pl.wntx1; w.ntiles1 = pl.wntiles1; w.nblk2 = pl.wnblk2;
-      // two kernels per sweep; counted as one sweep launch each
-      nlaunch[KIND_SWEEP]++;
+      // three kernels per sweep (gram, shifted sums, differences); counted as sweep launches
+      nlaunch[KIND_SWEEP] += 2;
       SGS_CUDA(launch(KIND_SWEEP, [&]() {
         return launch_wide<T>(w, pl.G, diag, g4 == SEGSALSA_G4_SIMPLEX, st);
       }));
@@ -1229,7 +1229,7 @@ class Solver : public SolverBase {
     } else {
       nlaunch[KIND_ROWF] += len; nlaunch[KIND_COL] += len; nlaunch[KIND_ROWI] += len;
     }
-    nlaunch[KIND_SWEEP] += pl.wide ? 2 * len : len;
+    nlaunch[KIND_SWEEP] += pl.wide ? 3 * len : len;
   }
   int enqueue_eager_iteration(cudaStream_t s) override {
     cudaStream_t keep = st;

@@ -16,13 +16,17 @@
 //     eq. (5) by a G-lane sum; then the new A, and the pixel-local MPOs of g1, g3, g4 with their
 //     duals and their part (u1 + d1) + (u3 + d3) + (u4 + d4) of the rhs.
 //
-//   k_wide_jt (one target pixel per G lanes): every target pixel m adds, shift by shift,
-//       w_h(m - s_j - e_h) - w_h(m - s_j) - w_v(m - s_j) + w_v(m - s_j - e_v)
-//     with w = omega_j (u + d2') = omega_j (v A + (v A - v)) recomputed from the stored v and A
-//     of each source pixel (J^T of eq. 12 as a gather, in a fixed order: deterministic). Nothing
-//     is written but the rhs, so the neighbouring targets' reads of the same entries do not
-//     race; they are served by L1 / L2. The result rhs = local part + J^T w is dense; the
-//     z-update reads it directly.
+//   J^T of eq. 12 on w = omega_j (u + d2') = omega_j (v A + (v A - v)), recomputed from the
+//   stored v and A: (J^T w)(m) = sum_j [w_h(m - s_j - e_h) - w_h(m - s_j)
+//   + w_v(m - s_j - e_v) - w_v(m - s_j)] = S_h(m - e_h) - S_h(m) + S_v(m - e_v) - S_v(m) with
+//   S(p) = sum_j w(p - s_j, j), the backward differences of one shifted sum per component:
+//
+//   k_wide_jt (one pixel per G lanes, over the gram tiles): S_h, S_v of every pixel, one v load
+//     and the A of the source (from a shared-memory window of the tile's sources) per shift, in
+//     a fixed order (deterministic); nothing but S is written, so the overlapping reads of v
+//     by neighbouring pixels do not race.
+//   k_wide_diff (one pixel and class per thread): rhs += S_h(m - e_h) - S_h(m) + S_v(m - e_v)
+//     - S_v(m). The result rhs = local part + J^T w is dense; the z-update reads it directly.
 //
 // Traced variants also accumulate ||d^{k+1} - d^k||^2 per tile (the gram kernel keeps the old
 // dual in a scratch buffer for a second pass) and write G^T d^{k+1} densely (dual residual).
@@ -43,7 +47,9 @@ struct WideArgs {
   T* dloc;           // [n][3][K]  (d1, d3, d4)
   T* V;              // [n][L][K][2]: the prior's last prox argument v (d2 = V (A - I))
   T* coef;           // [n][4]: A11, A12, A22 of that prox
-  T* scratch;        // DIAG: [n][L][K][2] the old dual d2 of the traced sweep
+  T* scratch;        // [n][L][K][2]: DIAG, the old dual d2 of the traced sweep (gram kernel);
+                     // then S = (S_h, S_v) [n][K][2] and, DIAG, the same sums of omega_j d2'
+                     // (transpose)
   T* rhs;            // [n][K] dense rhs (local part from the gram kernel, completed by k_wide_jt)
   T* gtd;            // DIAG: [n][K] dense G^T d^{k+1}
   double* diag_sq;   // DIAG: per-tile sums of squared dual changes
@@ -262,7 +268,7 @@ template <typename T, int G, bool DIAG>
 __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
   using V2 = typename Vec2Of<T>::type;
   constexpr int NC = 256 / G;
-  constexpr int UJ = 4;   // shifts whose V loads are issued together
+  constexpr int UJ = 8;   // shifts whose v loads are issued together
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int K = a.K, M = a.M, P = 2 * M + 1, L = a.L;
   const int EWc = NC + 2 * M + 1, EHc = 2 * M + 2;
@@ -273,20 +279,22 @@ __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
   int* woff = dyx + 2 * L;                                                    // [L]
   const int g = threadIdx.x % G, c = threadIdx.x / G;
   const V2* vv2 = reinterpret_cast<const V2*>(a.V);
+  V2* S = reinterpret_cast<V2*>(a.scratch);                                   // [n][K]
+  const size_t nK = (size_t)a.H * a.W * K;
   const long long LK = (long long)L * K;
   for (int j = threadIdx.x; j < L; j += blockDim.x) {
     const int jy = j / P, dy = jy - M, dx = j - jy * P - M;
     dyx[2 * j] = dy;
     dyx[2 * j + 1] = dx;
     offv[j] = (-(long long)dy * a.W - dx) * LK + (long long)j * K;   // V2 units, m - s_j
-    woff[j] = 4 * ((M + 1 - dy) * EWc + (M + 1 - dx));   // window entry of i0 (column 0)
+    woff[j] = 4 * ((M + 1 - dy) * EWc + (M + 1 - dx));   // window entry of m - s_j (column 0)
     om[j] = a.omega[j];
   }
   pdl_wait();  // v, A and the local rhs come from k_wide_gram
   for (int tile = blockIdx.x; tile < a.ntiles1; tile += gridDim.x) {
     const int y = tile / a.ntx1, x0 = (tile % a.ntx1) * NC;
     __syncthreads();  // the previous tile's window is no longer read
-    // A of the sources m - s_j - {0, e_h, e_v} of the tile's targets (periodic)
+    // A of the sources m - s_j of the tile's pixels (periodic)
     for (int idx = threadIdx.x; idx < EHc * EWc; idx += blockDim.x) {
       const int ry = idx / EWc, rx = idx - ry * EWc;
       const int py = wrap_idx(y - M - 1 + ry, a.H), px = wrap_idx(x0 - M - 1 + rx, a.W);
@@ -300,58 +308,77 @@ __global__ void __launch_bounds__(256) k_wide_jt(const WideArgs<T> a) {
     const int x = x0 + c;
     if (x >= a.W || g >= K) continue;   // no block-wide operation before the next tile's
     const long long m = (long long)y * a.W + x;
-    const bool inner = y >= M + 1 && y <= a.H - 1 - M && x >= M + 1 && x <= a.W - 1 - M;
-    T acc = T(0), accd = T(0);
+    const bool inner = y >= M && y <= a.H - 1 - M && x >= M && x <= a.W - 1 - M;
+    T sh = T(0), sv = T(0), dh = T(0), dv = T(0);
     for (int j0 = 0; j0 < L; j0 += UJ) {
-      V2 v0[UJ], vh[UJ], vv[UJ];
+      V2 v0[UJ];
 #pragma unroll
       for (int u = 0; u < UJ; ++u) {
         const int j = j0 + u;
         if (j >= L) break;
-        long long o0, oh, ov;
+        long long o0;
         if (inner) {
           o0 = m * LK + offv[j] + g;
-          oh = o0 - LK;
-          ov = o0 - (long long)a.W * LK;
         } else {
-          // i0 = m - s_j, ih = i0 - e_h, iv = i0 - e_v (periodic; |s_j| <= M < H, W)
-          int ys = y - dyx[2 * j], xs = x - dyx[2 * j + 1];
+          int ys = y - dyx[2 * j], xs = x - dyx[2 * j + 1];   // m - s_j, periodic
           ys += (ys < 0) ? a.H : 0;
           ys -= (ys >= a.H) ? a.H : 0;
           xs += (xs < 0) ? a.W : 0;
           xs -= (xs >= a.W) ? a.W : 0;
-          const int xh = xs == 0 ? a.W - 1 : xs - 1, yv = ys == 0 ? a.H - 1 : ys - 1;
           o0 = (((long long)ys * a.W + xs) * L + j) * K + g;
-          oh = (((long long)ys * a.W + xh) * L + j) * K + g;
-          ov = (((long long)yv * a.W + xs) * L + j) * K + g;
         }
         v0[u] = vv2[o0];
-        vh[u] = vv2[oh];
-        vv[u] = vv2[ov];
       }
 #pragma unroll
       for (int u = 0; u < UJ; ++u) {
         const int j = j0 + u;
         if (j >= L) break;
-        // window entry of i0 (the window starts at (y - M - 1, x0 - M - 1))
-        const T* p0 = cw + woff[j] + 4 * c;
-        const Coef4<T> c0 = Coef4<T>::at(p0), ch = Coef4<T>::at(p0 - 4),
-                       cv = Coef4<T>::at(p0 - 4 * EWc);
-        const T u0x = prox_h(v0[u].x, v0[u].y, c0.a11, c0.a12);
-        const T u0y = prox_v(v0[u].x, v0[u].y, c0.a12, c0.a22);
-        const T n0x = u0x - v0[u].x, n0y = u0y - v0[u].y;
-        const T uhx = prox_h(vh[u].x, vh[u].y, ch.a11, ch.a12);
-        const T nhx = uhx - vh[u].x;
-        const T uvy = prox_v(vv[u].x, vv[u].y, cv.a12, cv.a22);
-        const T nvy = uvy - vv[u].y;
+        const Coef4<T> c0 = Coef4<T>::at(cw + woff[j] + 4 * c);
+        const T ux = prox_h(v0[u].x, v0[u].y, c0.a11, c0.a12);
+        const T uy = prox_v(v0[u].x, v0[u].y, c0.a12, c0.a22);
+        const T nx = ux - v0[u].x, ny = uy - v0[u].y;
         const T o = om[j];
-        acc += o * (uhx + nhx) - o * (u0x + n0x) - o * (u0y + n0y) + o * (uvy + nvy);
-        if constexpr (DIAG) accd += o * nhx - o * n0x - o * n0y + o * nvy;
+        sh += o * (ux + nx);
+        sv += o * (uy + ny);
+        if constexpr (DIAG) {
+          dh += o * nx;
+          dv += o * ny;
+        }
       }
     }
     const size_t oo = (size_t)m * K + g;
-    a.rhs[oo] += acc;
-    if constexpr (DIAG) a.gtd[oo] += accd;
+    V2 r;
+    r.x = sh; r.y = sv;
+    S[oo] = r;
+    if constexpr (DIAG) {
+      r.x = dh; r.y = dv;
+      S[nK + oo] = r;
+    }
+  }
+  pdl_trigger();
+}
+
+// rhs(m) += S_h(m - e_h) - S_h(m) + S_v(m - e_v) - S_v(m) (and the same for G^T d2' into gtd).
+template <typename T, bool DIAG>
+__global__ void __launch_bounds__(256) k_wide_diff(const WideArgs<T> a) {
+  using V2 = typename Vec2Of<T>::type;
+  const V2* S = reinterpret_cast<const V2*>(a.scratch);
+  const int K = a.K;
+  const size_t nK = (size_t)a.H * a.W * K;
+  pdl_wait();  // S comes from k_wide_jt
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nK;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / K;
+    const int k = (int)(i - pix * K);
+    const int y = (int)(pix / a.W), x = (int)(pix - (size_t)y * a.W);
+    const size_t ih = ((size_t)y * a.W + (x == 0 ? a.W - 1 : x - 1)) * K + k;
+    const size_t iv = ((size_t)(y == 0 ? a.H - 1 : y - 1) * a.W + x) * K + k;
+    const V2 s0 = S[i], shv = S[ih], svv = S[iv];
+    a.rhs[i] += (shv.x - s0.x) + (svv.y - s0.y);
+    if constexpr (DIAG) {
+      const V2 d0 = S[nK + i], dhv = S[nK + ih], dvv = S[nK + iv];
+      a.gtd[i] += (dhv.x - d0.x) + (dvv.y - d0.y);
+    }
   }
   pdl_trigger();
 }

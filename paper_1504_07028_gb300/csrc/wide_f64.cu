@@ -22,7 +22,11 @@ static cudaError_t wide_g(const WideArgs<double>& a, cudaStream_t st) {
   if (st == reinterpret_cast<cudaStream_t>(-1)) return cudaSuccess;  // grants only
   if ((e = launch_pdl(k_wide_gram<double, G, DIAG, SIMP>, dim3(a.ntiles1), dim3(256), s1, st, a)) != cudaSuccess)
     return e;
-  return launch_pdl(k_wide_jt<double, G, DIAG>, dim3(a.nblk2), dim3(256), s2, st, a);
+  if ((e = launch_pdl(k_wide_jt<double, G, DIAG>, dim3(a.nblk2), dim3(256), s2, st, a)) != cudaSuccess)
+    return e;
+  const size_t nK = (size_t)a.H * a.W * a.K;
+  const int nb3 = (int)std::min<size_t>((nK + 255) / 256, 152 * 8);
+  return launch_pdl(k_wide_diff<double, DIAG>, dim3(nb3), dim3(256), 0, st, a);
 }
 
 template <int G>
