@@ -173,10 +173,12 @@ int segsalsa_str_set_weights(segsalsa_str_t* h, const double* weights);
  * Jacobians applied per pixel, and the adjoint of J is J^T. Device memory for the checkpoints
  * and one segment's states is allocated for the call and released before it returns. The
  * handle ends at iteration `iters`, as after set_probs + solve(iters).
- * Covers Schatten p = 1 and 2 with g4 on the affine set and patches up to 5x5 (M <= 2);
- * SEGSALSA_ERR_ARG otherwise. The
+ * Covers Schatten p = 1, 2 and infinity, g4 on the affine set or on the probability simplex
+ * (set_g4), and patches up to 5x5 (M <= 2); SEGSALSA_ERR_ARG for wider patches. The
  * derivative is that of the iteration as written: at points where an MPO switches case (a
- * singular value equal to tau, a component of v3 equal to 0) one side's derivative is taken. */
+ * singular value equal to tau, the two shrunk singular values of p = infinity meeting, a
+ * component of v3 equal to 0, a class entering the simplex projection's active set) one
+ * side's derivative is taken. */
 int segsalsa_str_backward(segsalsa_str_t* h, int32_t iters, const void* zbar, int32_t layout,
                           void* grad_logp, double* grad_lambda, double* grad_weights,
                           int32_t checkpoint_every, int32_t on_device);

@@ -103,6 +103,7 @@ struct AdjArgs {
   const T* omega;
   T tau, mu, invK;
   int sp;
+  int simplex;        // g4 on the probability simplex (else on the affine set 1^T xi = 1)
 };
 
 constexpr int ADJ_THREADS = 256;
@@ -200,12 +201,32 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_adj_vjp(const AdjArgs<T> a) 
     const T pbar = ub1 / (a.mu * t) - su / (a.mu * t * t) * dtdp;
     a.glogp[e] += pk * pbar;
   }
-  // block 3 (positive orthant) and block 4 (affine set)
+  // block 3 (positive orthant) and block 4 (affine set, or the probability simplex)
   const T ub3 = T(2) * bc - nd3;
   const T vb3 = -bc + nd3 + ((v3 > T(0)) ? ub3 : T(0));
   const T ub4 = T(2) * bc - nd4;
-  const T sub4 = group_sum<G>(kok ? ub4 : T(0));
-  const T vb4 = -bc + nd4 + (ub4 - sub4 * a.invK);
+  T vb4;
+  if (!a.simplex) {
+    const T sub4 = group_sum<G>(kok ? ub4 : T(0));
+    vb4 = -bc + nd4 + (ub4 - sub4 * a.invK);
+  } else {
+    // the projection max(v4 - theta, 0) moves the active classes S = {v4 > theta} by a
+    // common shift: its Jacobian is I - 1 1^T / |S| on S and 0 elsewhere. The active set by
+    // the sweep's fixed-point search (Michelot), in the same arithmetic.
+    bool act = kok;
+    for (int pass = 0; pass < 32; ++pass) {
+      const T cnt = group_sum<G>(act ? T(1) : T(0));
+      const T sum = group_sum<G>(act ? v4 : T(0));
+      const T theta = (cnt > T(0)) ? (sum - T(1)) / cnt : T(0);
+      const bool nact = act && (v4 > theta);
+      const bool changed = nact != act;
+      act = nact;
+      if (!__any_sync(0xffffffffu, changed)) break;
+    }
+    const T cnt = group_sum<G>(act ? T(1) : T(0));
+    const T sub4 = group_sum<G>(act ? ub4 : T(0));
+    vb4 = -bc + nd4 + (act ? ub4 - sub4 / cnt : T(0));
+  }
   (void)s4;
   // block 2 (Schatten prox): ubar2 = 2 J bbar - vbar2^{k+1}
   T jbh[L], jbv[L];

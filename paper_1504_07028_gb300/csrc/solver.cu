@@ -1328,9 +1328,7 @@ class Solver : public SolverBase {
     if (every < 1) return fail(SEGSALSA_ERR_ARG, "checkpoint_every must be >= 1");
     if (!zbar || !glogp) return fail(SEGSALSA_ERR_ARG, "zbar and grad_logp are required");
     if (layout != SEGSALSA_LAYOUT_KHW && layout != SEGSALSA_LAYOUT_HWK) return fail(SEGSALSA_ERR_ARG, "bad layout");
-    if (sp == 0) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers Schatten p = 1 and 2");
     if (pl.wide) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers patches up to 5 x 5 (M <= 2)");
-    if (g4 != SEGSALSA_G4_AFFINE) return fail(SEGSALSA_ERR_ARG, "the reverse pass covers g4 on the affine set");
     const int K = pl.K, L = pl.L, n = pl.n;
     const size_t nK = (size_t)n * K, nloc = 3 * nK, n2 = 2 * (size_t)L * nK;
     const size_t tslot = (size_t)pl.ntiles * pl.EHmax * pl.EWmax * K;
@@ -1449,6 +1447,7 @@ class Solver : public SolverBase {
         a.mu = (T)mu;
         a.invK = (T)(1.0 / K);
         a.sp = sp;
+        a.simplex = g4 == SEGSALSA_G4_SIMPLEX ? 1 : 0;
         SGS_LAUNCH(KIND_ADJ, launch_adj_vjp<T>(a, pl.M, pl.G, blocks, st));
         // the unit's block partials into the running FP64 sums; units run in the order
         // k = iters - 1 .. 1 whatever the checkpoint interval, so the sums are too

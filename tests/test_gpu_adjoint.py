@@ -80,22 +80,64 @@ def test_fp32_backward_close_to_fp64(B):
     assert abs(l32 - l64) < 2e-3 * scale and np.abs(o32 - o64).max() < 2e-3 * scale
 
 
+@pytest.mark.parametrize("H,W,K,M,sp,g4,T,C", [
+    (12, 14, 3, 1, "inf", "affine", 7, 3), (11, 13, 5, 2, "inf", "affine", 5, 2),
+    (12, 14, 3, 1, 1, "simplex", 7, 3), (10, 9, 4, 0, 2, "simplex", 6, 4),
+    (9, 16, 9, 1, "inf", "simplex", 8, 10)])
+def test_fp64_backward_inf_and_simplex_match_reference(B, H, W, K, M, sp, g4, T, C):
+    """Schatten p = infinity (the Moreau form of the prox) and g4 on the probability simplex
+    (active set recomputed in the reverse pass) against the reference gradient; in the simplex
+    cases classes leave the active set (the affine-set gradient differs)."""
+    logp, zbar = _case(H, W, K, 90 + H + K)
+    s = _mk(B, H, W, K, M, sp, "fp64")
+    if g4 == "simplex":
+        s.set_g4("simplex")
+    om = O.gaussian_weights(M, 0.5 if M <= 1 else 1.0)
+    s.set_log_probs(logp)
+    g, glam, gom = s.backward(T, zbar, checkpoint_every=C)
+    spo = np.inf if sp == "inf" else sp
+    r_lp, r_lam, r_om, r_z = U.reference_gradient(logp, 1.2, om, M, 1.0, spo, T, zbar, g4)
+    scale = max(np.abs(r_lp).max(), abs(r_lam), np.abs(r_om).max())
+    assert np.abs(g - r_lp).max() < 1e-8 * scale
+    assert abs(glam - r_lam) < 1e-8 * scale
+    assert np.abs(gom - r_om).max() < 1e-8 * scale
+    assert s.get_iteration() == T
+    assert np.abs(s.get_z() - r_z).max() < 1e-10
+    if g4 == "simplex":   # the active set matters: the affine-set gradient is another one
+        a_lp = U.reference_gradient(logp, 1.2, om, M, 1.0, spo, T, zbar, "affine")[0]
+        assert np.abs(a_lp - r_lp).max() > 1e-3 * scale
+    s.close()
+
+
+def test_fp32_backward_inf_simplex_close_to_fp64(B):
+    logp, zbar = _case(24, 20, 6, 86)
+    out = {}
+    for prec, dt in (("fp64", np.float64), ("fp32", np.float32)):
+        s = _mk(B, 24, 20, 6, 1, "inf", prec)
+        s.set_g4("simplex")
+        s.set_log_probs(logp.astype(dt))
+        out[prec] = s.backward(12, zbar.astype(dt), checkpoint_every=5)
+        s.close()
+    g64, l64, o64 = out["fp64"]
+    g32, l32, o32 = out["fp32"]
+    scale = max(np.abs(g64).max(), abs(l64), np.abs(o64).max())
+    assert np.abs(g32 - g64).max() < 2e-3 * scale
+    assert abs(l32 - l64) < 2e-3 * scale and np.abs(o32 - o64).max() < 2e-3 * scale
+
+
 def test_backward_rejects_unsupported(B):
-    logp, zbar = _case(8, 8, 3, 82)
-    s = _mk(B, 8, 8, 3, 1, "inf", "fp64")
+    logp, zbar = _case(14, 14, 3, 82)
+    s = _mk(B, 8, 8, 3, 1, 1, "fp64")
+    s.set_log_probs(np.ascontiguousarray(logp[:, :8, :8]))
+    with pytest.raises(B.SegsalsaError) as e:
+        s.backward(0, np.ascontiguousarray(zbar[:, :8, :8]))
+    assert e.value.code == B.SEGSALSA_ERR_ARG
+    s.close()
+    s = _mk(B, 14, 14, 3, 3, 1, "fp64", sigma=1.5)
     s.set_log_probs(logp)
     with pytest.raises(B.SegsalsaError) as e:
         s.backward(3, zbar)
     assert e.value.code == B.SEGSALSA_ERR_ARG
-    s.close()
-    s = _mk(B, 8, 8, 3, 1, 1, "fp64")
-    s.set_log_probs(logp)
-    s.set_g4("simplex")
-    with pytest.raises(B.SegsalsaError):
-        s.backward(3, zbar)
-    s.set_g4("affine")
-    with pytest.raises(B.SegsalsaError):
-        s.backward(0, zbar)
     s.close()
 
 
