@@ -454,6 +454,19 @@ def run_ours(args, rank, world, local_rank):
     launches = 0
     for _, s in solvers:
         launches += sum(c for c, _ in s.kernel_stats().values())
+    # each solve alone, CUDA-graph replay as in the timed steps (events on its own stream): the
+    # time per iteration of one image without the overlap of the concurrent solves
+    single_us = []
+    if not args.profile_run:
+        for (cfg, s), sx in zip(solvers, streams):
+            s.set_probs(p_dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(sx)
+            s.solve(cfg.iters, trace_every=10)
+            b.record(sx)
+            b.synchronize()
+            single_us.append(1e3 * a.elapsed_time(b) / cfg.iters)
     # per-kernel device times: CUDA events around every launch, recorded on the launch stream
     # during a replay of the same steps (the events add ~1 us gaps, so they stay out of `value`)
     for _, s in solvers:
@@ -489,6 +502,8 @@ def run_ours(args, rank, world, local_rank):
             "sweep_us": m_sw / n_sw * 1e3, "sweep_gbs": sb / (m_sw / n_sw * 1e-3) / 1e9,
             "sweep_frac_of_hbm": sb / (m_sw / n_sw * 1e-3) / 1e9 / hbm_peak,
             "kernel_ms_per_iteration": sum(m for _, m in st.values()) / (args.steps * cfg.iters)})
+        if single_us:
+            per_solve[-1]["graph_us_per_iteration_alone"] = single_us[len(per_solve) - 1]
         s.set_profiling(args.profile_run)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     sweep_bytes, iter_bytes = solvers[0][1].traffic_model()
@@ -592,10 +607,14 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": sw_bytes_tot / sw_cnt,
                      "avg_launch_us": sw_ms / sw_cnt * 1e3},
         "kernel_ms": {k: {"launches": c, "ms": round(m, 4)} for k, (c, m) in stats.items()},
+        "us_per_iteration_one_solve_alone": (sum(single_us) / len(single_us)) if single_us else None,
         "per_solve": per_solve,
         "kernel_timing": ("CUDA events around every launch on the launch stream, in a replay "
                           f"of the {args.steps} timed steps with the solves run one at a time "
-                          f"({prof_ms:.1f} ms with the events)"),
+                          f"({prof_ms:.1f} ms with the events; the events break the programmatic "
+                          "dependent launches and add gaps, so kernel_ms overstates the "
+                          "iteration: us_per_iteration_one_solve_alone is the graph-replay time "
+                          "of one solve)"),
         "dominant_kernel": dom[0],
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "ADMM iter/s", "h2d_bytes_per_step": h2d,
@@ -603,11 +622,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": ck,
         "cpu_baseline": cpu,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for _, s in solvers:
         s.close()
     pool.shutdown()
+    return line if rank == 0 else None
 
 
 def run_batch(args, rank, world, local_rank):
@@ -1146,13 +1164,54 @@ def run_reference_diff(args):
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
+DEFAULT_WORKLOAD = "2048x2048"
+# short runs of the other workloads appended to the default line (keys kept per workload)
+EXTRAS = [("145x145", ["--steps", "5", "--warmup", "3"]),
+          ("batch64", ["--steps", "3", "--warmup", "3"]),
+          ("mlr610x340", ["--steps", "3", "--warmup", "3"]),
+          ("patchsweep", ["--steps", "2", "--warmup", "3"])]
+EXTRA_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "us_per_iteration_one_solve_alone",
+              "gpu_launches", "clocks")
+
+
+def run_extras():
+    """Each other workload in a child process of this script (fresh handles and memory, the
+    same GPU), without the CPU baseline and the FP64 check; a compact summary of its line."""
+    out = {}
+    for name, extra in EXTRAS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--skip-cpu",
+               "--skip-fp64-check", *extra]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+            ln = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode != 0 or not ln:
+                out[name] = {"error": (r.stderr.strip().splitlines() or ["no output"])[-1][:200]}
+                continue
+            d = json.loads(ln[-1])
+            rec = {k: d[k] for k in EXTRA_KEYS if k in d}
+            rec["workload"] = d.get("config", {}).get("workload")
+            if "roofline" in d:
+                rec["roofline"] = {k: d["roofline"].get(k) for k in
+                                   ("kernel", "achieved", "peak", "unit", "frac")}
+            if "e2e" in d:
+                rec["e2e"] = d["e2e"]
+            if "per_solve" in d:
+                rec["per_solve"] = d["per_solve"]
+            out[name] = rec
+        except Exception as e:  # a failed extra never costs the headline line
+            out[name] = {"error": str(e)[:200]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2048x2048",
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the short runs of the other workloads")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     help="2048x2048 (default), 145x145, 64x64, HxW (K=16 synthetic scene), patchsweep, or "
                          "batch64 (64 uneven images in one batch), mlr610x340 (MLR front end), or diff256 "
                          "(differentiable solver)")
@@ -1186,7 +1245,12 @@ def main():
         elif args.workload == "diff256":
             run_diff(args, rank, world, local_rank)
         else:
-            run_ours(args, rank, world, local_rank)
+            line = run_ours(args, rank, world, local_rank)
+            if line is not None:
+                if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_extras \
+                        and not args.profile_run:
+                    line["other_workloads"] = run_extras()
+                print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch
