@@ -340,50 +340,67 @@ inline cudaError_t launch_prior(int M, int G, int blocks, cudaStream_t st, const
 }
 
 // One trace record (k, primal, dual, objective, min z, max |1^T z - 1|), reducing the block
-// partials in a fixed order. One warp: each lane sums a strided subset in FP64 (four independent
-// chains), then shuffles; no block barriers (the partials number a few hundred to a few
-// thousand, and FP64 is a narrow pipe on this part).
-__global__ void __launch_bounds__(32) k_finalize_trace(
+// partials in a fixed order: FT_THREADS threads each sum a strided subset in FP64 (four
+// independent chains, so that loads are in flight together: one warp took 79 us for the 16384
+// tile partials of a 2048 x 2048 image, bound by load latency), then a fixed shuffle tree per
+// warp and the warp results in warp order.
+constexpr int FT_THREADS = 1024;
+
+__global__ void __launch_bounds__(FT_THREADS) k_finalize_trace(
     const double* sq, int nsq, const double* proj, int nproj, const double* prior, int nprior,
     double k, double mu, double lambda, double* rec) {
-  const int l = threadIdx.x;
+  __shared__ double red[6][FT_THREADS / 32];
+  const int t = threadIdx.x, l = t & 31, w = t >> 5;
   auto sum = [&](const double* v, int n, int stride, int off) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i0 = l; i0 < n; i0 += 4 * 32) {
+    for (int i0 = t; i0 < n; i0 += 4 * FT_THREADS) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int i = i0 + 32 * u;
+        const int i = i0 + FT_THREADS * u;
         if (i < n) acc[u] += v[stride * i + off];
       }
     }
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
   };
   pdl_wait();
-  double a = sum(sq, nsq, 1, 0);
-  double b = sum(proj, nproj, 4, 3);
-  double c = sum(proj, nproj, 4, 2);
-  double d = sum(prior, nprior, 1, 0);
-  double mn = 1e300, mx = 0.0;
-  for (int i = l; i < nproj; i += 32) {
-    mn = fmin(mn, proj[4 * i]);
-    mx = fmax(mx, proj[4 * i + 1]);
+  double v[6];
+  v[0] = sum(sq, nsq, 1, 0);
+  v[1] = sum(proj, nproj, 4, 3);
+  v[2] = sum(proj, nproj, 4, 2);
+  v[3] = sum(prior, nprior, 1, 0);
+  v[4] = 1e300;
+  v[5] = 0.0;
+  for (int i = t; i < nproj; i += FT_THREADS) {
+    v[4] = fmin(v[4], proj[4 * i]);
+    v[5] = fmax(v[5], proj[4 * i + 1]);
   }
+  auto tree = [&](double (&x)[6]) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-    d += __shfl_xor_sync(0xffffffffu, d, o);
-    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  if (l == 0) {
-    rec[0] = k;
-    rec[1] = sqrt(a);
-    rec[2] = mu * sqrt(b);
-    rec[3] = c + lambda * d;
-    rec[4] = mn;
-    rec[5] = mx;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+      x[4] = fmin(x[4], __shfl_xor_sync(0xffffffffu, x[4], o));
+      x[5] = fmax(x[5], __shfl_xor_sync(0xffffffffu, x[5], o));
+    }
+  };
+  tree(v);
+  if (l == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q][w] = v[q];
+  __syncthreads();
+  if (w == 0) {
+    double x[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) x[q] = red[q][l];
+    tree(x);
+    if (l == 0) {
+      rec[0] = k;
+      rec[1] = sqrt(x[0]);
+      rec[2] = mu * sqrt(x[1]);
+      rec[3] = x[2] + lambda * x[3];
+      rec[4] = x[4];
+      rec[5] = x[5];
+    }
   }
 }
 

@@ -800,7 +800,7 @@ class Solver : public SolverBase {
     const int n = pl.n, K = pl.K;
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_project_g<T>(pl.G, pl.nproj_blk, st, b.z, b.p, b.zp, n, K, (const T*)b.P2, pl.wide ? (const T*)b.P2 : nullptr, (const int*)b.covY, (const int*)b.offX, pl.W, pl.ntx, pl.EHmax, pl.EWmax, b.dproj); }));
     SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_prior<T>(pl.M, pl.G, pl.nprior_blk, st, b.zp, b.omega, pl.H, pl.W, K, sp, b.dprior); }));
-    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(32), 0, st, (const double*)b.dsq, pl.wide ? pl.wntiles1 : pl.ntiles, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
+    SGS_CUDA(launch(KIND_DIAG, [&]() { return launch_pdl(k_finalize_trace, dim3(1), dim3(FT_THREADS), 0, st, (const double*)b.dsq, pl.wide ? pl.wntiles1 : pl.ntiles, (const double*)b.dproj, pl.nproj_blk, (const double*)b.dprior, pl.nprior_blk, (double)k, mu, lambda, b.dtrace + 6 * rec); }));
     return SEGSALSA_OK;
   }
 
