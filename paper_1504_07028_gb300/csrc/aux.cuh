@@ -69,6 +69,17 @@ __global__ void k_labels(const T* z, int n, int K, int32_t* lab) {
   lab[i] = arg;
 }
 
+// v mod n for v >= -n: one conditional correction in the common case, a division only when v
+// is two periods or more past the end (halo entries of a partial tile on a narrow image).
+__device__ __forceinline__ int wrap_near(int v, int n) {
+  if (v < 0) v += n;
+  if (v >= n) {
+    v -= n;
+    if (v >= n) v %= n;
+  }
+  return v;
+}
+
 // G consecutive values of a pixel's classes (K valid, the rest zero): 16-byte loads when the
 // row of K values is 16-byte aligned and a whole number of vectors, scalar loads otherwise.
 template <typename T, int G>
@@ -135,10 +146,47 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
   T vmin = T(1e30), vdev = T(0), vdata = T(0), vgsq = T(0);
   const uint32_t all = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
   pdl_wait();
+  constexpr int VE = 16 / sizeof(T);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     T v[G], pk[G];
     load_classes<T, G>(z + (size_t)i * K, K, v);
     load_classes<T, G>(p + (size_t)i * K, K, pk);
+    // ||G^T d||^2 first: its loads do not depend on the projection, so they are in flight
+    // together with those of z and p
+    if (gtd) {
+#pragma unroll
+      for (int k0 = 0; k0 < G; k0 += VE) {
+        if (k0 >= K) break;
+        T gd[VE];
+        load_chunk<T>(gtd + (size_t)i * K, k0, K, gd);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) vgsq += gd[e] * gd[e];
+      }
+    } else {
+      // G^T d at pixel i: the (at most 2 x 2) covering partials, in the row pass's order
+      const int y = i / W, x = i - y * W;
+      const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
+      const int rb0 = (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
+      const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
+      const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
+#pragma unroll
+      for (int k0 = 0; k0 < G; k0 += VE) {
+        if (k0 >= K) break;
+        T g00[VE], g01[VE], g10[VE], g11[VE];
+        load_chunk<T>(P2 + rb0 + o0, k0, K, g00);
+        if (o1 >= 0) load_chunk<T>(P2 + rb0 + o1, k0, K, g01);
+        if (rb1 >= 0) load_chunk<T>(P2 + rb1 + o0, k0, K, g10);
+        if (rb1 >= 0 && o1 >= 0) load_chunk<T>(P2 + rb1 + o1, k0, K, g11);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+          T gd = g00[e];
+          if (o1 >= 0) gd += g01[e];
+          if (rb1 >= 0) gd += g10[e];
+          if (rb1 >= 0 && o1 >= 0) gd += g11[e];
+          vgsq += gd * gd;
+        }
+      }
+    }
     T s = T(0), mn = v[0];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
@@ -160,54 +208,31 @@ __global__ void __launch_bounds__(AUX_THREADS) k_project(const T* z, const T* p,
       if (nact == act) break;
       act = nact;
     }
-    T pz = T(0);
-    T* zo = zp + (size_t)i * K;
+    T pz = T(0), q[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-      const T q = fmax(v[k] - theta, T(0));
-      if (k < K) {
-        zo[k] = q;
-        pz += pk[k] * q;
+      q[k] = fmax(v[k] - theta, T(0));
+      if (k < K) pz += pk[k] * q[k];
+    }
+    // the projection out in 16-byte vectors where the pixel's row allows it
+    T* zo = zp + (size_t)i * K;
+    if (K % VE == 0 && (reinterpret_cast<uintptr_t>(zo) & 15) == 0) {
+#pragma unroll
+      for (int k0 = 0; k0 < G; k0 += VE) {
+        if (k0 >= K) break;
+        if constexpr (sizeof(T) == 4)
+          *reinterpret_cast<float4*>(zo + k0) = make_float4(q[k0], q[k0 + 1], q[k0 + 2], q[k0 + 3]);
+        else
+          *reinterpret_cast<double2*>(zo + k0) = make_double2(q[k0], q[k0 + 1]);
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < G; ++k)
+        if (k < K) zo[k] = q[k];
     }
     vmin = fmin(vmin, mn);
     vdev = fmax(vdev, fabs(s - T(1)));
     vdata -= log(pz);
-    constexpr int VE = 16 / sizeof(T);
-    if (gtd) {
-#pragma unroll
-      for (int k0 = 0; k0 < G; k0 += VE) {
-        if (k0 >= K) break;
-        T gd[VE];
-        load_chunk<T>(gtd + (size_t)i * K, k0, K, gd);
-#pragma unroll
-        for (int e = 0; e < VE; ++e) vgsq += gd[e] * gd[e];
-      }
-      continue;
-    }
-    // G^T d at pixel i: the (at most 2 x 2) covering partials, in the row pass's order
-    const int y = i / W, x = i - y * W;
-    const int c0 = covY[2 * y], c1 = covY[2 * y + 1];
-    const int rb0 = (((c0 >> 16) * ntx * EHmax) + (c0 & 0xffff)) * EWmax * K;
-    const int rb1 = c1 < 0 ? -1 : (((c1 >> 16) * ntx * EHmax) + (c1 & 0xffff)) * EWmax * K;
-    const int o0 = offX[2 * x], o1 = offX[2 * x + 1];
-#pragma unroll
-    for (int k0 = 0; k0 < G; k0 += VE) {
-      if (k0 >= K) break;
-      T g00[VE], g01[VE], g10[VE], g11[VE];
-      load_chunk<T>(P2 + rb0 + o0, k0, K, g00);
-      if (o1 >= 0) load_chunk<T>(P2 + rb0 + o1, k0, K, g01);
-      if (rb1 >= 0) load_chunk<T>(P2 + rb1 + o0, k0, K, g10);
-      if (rb1 >= 0 && o1 >= 0) load_chunk<T>(P2 + rb1 + o1, k0, K, g11);
-#pragma unroll
-      for (int e = 0; e < VE; ++e) {
-        T gd = g00[e];
-        if (o1 >= 0) gd += g01[e];
-        if (rb1 >= 0) gd += g10[e];
-        if (rb1 >= 0 && o1 >= 0) gd += g11[e];
-        vgsq += gd * gd;
-      }
-    }
   }
   const double a = block_min_w<T>(vmin, red32);
   if (threadIdx.x == 0) part[4 * blockIdx.x + 0] = a;
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* ome
     __syncthreads();  // the previous tile's reads of sA/sB/sC are done (and w2 is written)
     for (int r = threadIdx.x; r < RH * RW; r += blockDim.x) {
       const int ry = r / RW, rx = r - ry * RW;
-      const int y = wrap_idx(y0 - M + ry, H), x = wrap_idx(x0 - M + rx, W);
+      const int y = wrap_near(y0 - M + ry, H), x = wrap_near(x0 - M + rx, W);  // M < H, W
       const int xh = x + 1 == W ? 0 : x + 1, yv = y + 1 == H ? 0 : y + 1;
       constexpr int VE = 16 / sizeof(T);
       const T* rc = zp + ((size_t)y * W + x) * K;
