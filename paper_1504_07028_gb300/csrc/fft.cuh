@@ -1260,13 +1260,25 @@ __device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T
   constexpr int NB = N / R;
   constexpr int ITEMS = NB * B;
   constexpr int STRIDE = NB / NS;
+  // a butterfly's R inputs (outputs) are NB * B (NS * B) elements apart: where that is a whole
+  // number of pad periods, the padded slots differ by a constant, so one padded base address
+  // and immediate offsets replace R index computations (same slots, same results)
+  constexpr int PP = 1 << PadShift<T>::v;
+  constexpr bool IN_CONST = (NB * B) % PP == 0, OUT_CONST = (NS * B) % PP == 0;
+  constexpr int SI = NB * B + NB * B / PP, SO = NS * B + NS * B / PP;
   for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
     const int t = it / B, b = it - t * B;
     const int g = t / NS;
     const int j = t - g * NS;
     C v[R];
+    if constexpr (IN_CONST) {
+      const C* xi = Xin + px<T>(t * B + b);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * NB) * B + b)];
+      for (int r = 0; r < R; ++r) v[r] = xi[r * SI];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * NB) * B + b)];
+    }
     if constexpr (NS > 1) {
       const C w1 = tw[j * STRIDE];
       v[1] = cmul(v[1], w1);
@@ -1288,8 +1300,14 @@ __device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T
     }
     Dft<R, C>::run(v);
     const int base = (g * NS * R + j) * B + b;
+    if constexpr (OUT_CONST) {
+      C* xo = Xout + px<T>(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) Xout[px<T>(base + r * NS * B)] = v[r];
+      for (int r = 0; r < R; ++r) xo[r * SO] = v[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) Xout[px<T>(base + r * NS * B)] = v[r];
+    }
   }
 }
 
