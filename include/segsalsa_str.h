@@ -67,14 +67,20 @@ enum { SEGSALSA_G4_AFFINE = 0, SEGSALSA_G4_SIMPLEX = 1 }; /* segsalsa_str_set_g4
 
 /* Problem statement of eq. (7) and the SALSA penalty of eq. (13). */
 typedef struct {
-  int32_t H, W;          /* image size; H, W >= 2M+2                                      */
+  int32_t H, W;          /* image size; H, W >= 2M+2. The row transform length (W when its
+                            prime factors are at most 103, else the Bluestein length, a
+                            7-smooth length >= 2W - 1) must be <= 8192, so W <= 8192 for such
+                            W and about W <= 4096 otherwise; the column solve holds H rows of
+                            a complex column in shared memory: H <= 25600 (FP32), 12800
+                            (FP64). SEGSALSA_ERR_ARG outside these limits.                 */
   int32_t K;             /* number of classes, 2 <= K <= 32                               */
   int32_t M;             /* patch half-width: (2M+1)x(2M+1) patch, 0 <= M <= 5 (1x1 up to
                             the 11x11 patch of Sec. 5's patch-size study). M = 0 is the 1x1
                             patch, i.e. SegSALSA with the VTV prior (Sec. 3). M <= 2 runs the
-                            fused one-launch sweep; M >= 3 a two-launch sweep (per-pixel Gram
-                            matrix and prox coefficients, then J^T as a gather) that needs a
-                            second d2-sized buffer for u2 + d2 (see workspace_bytes)        */
+                            fused one-launch sweep; M >= 3 a three-launch sweep that keeps the
+                            prior's dual as the last prox argument and a 2x2 matrix per pixel
+                            (get_state writes d2 itself) and needs a second d2-sized scratch
+                            buffer (see workspace_bytes)                                    */
   const double* weights; /* L = (2M+1)^2 shift weights omega_j (row-major over (dy, dx)),
                             host memory, copied at creation; NULL selects the Gaussian
                             omega_j = sqrt(g_j), g_j = exp(-|s_j|^2/(2 sigma^2)) / sum        */

@@ -49,7 +49,13 @@ def test_params_struct_matches_header():
     (dict(H=8, W=8, K=4, lam=-1.0), False), (dict(H=8, W=8, K=4, mu=0.0), False),
     (dict(H=8, W=8, K=4, schatten_p=3), False), (dict(H=8, W=8, K=4, sigma=0.0), False),
     (dict(H=2, W=2, K=4, M=0), True), (dict(H=2048, W=2048, K=16), True),
-    (dict(H=30000, W=8, K=4), False), (dict(H=8, W=9000, K=4), False)])
+    (dict(H=30000, W=8, K=4), False), (dict(H=8, W=9000, K=4), False),
+    # the documented row-transform and column-solve limits
+    (dict(H=8, W=8192, K=4), True), (dict(H=8, W=8137, K=4), True), (dict(H=8, W=8191, K=4), False),
+    (dict(H=8, W=4093, K=4), True), (dict(H=8, W=4099, K=4), False),
+    (dict(H=25600, W=8, K=4), True), (dict(H=25601, W=8, K=4), False),
+    (dict(H=12800, W=8, K=4, precision="fp64"), True),
+    (dict(H=12801, W=8, K=4, precision="fp64"), False)])
 def test_parameter_checks(lib, kw, ok):
     pr = B.make_params(**kw)
     if ok:
