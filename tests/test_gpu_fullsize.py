@@ -155,3 +155,28 @@ def test_145x145_k16_300_iterations_against_oracle(B, oracle_refs, sp):
     assert np.array_equal(lab, np.argmax(z, axis=0))
     # residuals, objective, feasibility of the trace records: FP64 sums of FP32 iterates
     assert np.allclose(tr[:, 1:4], tro[:, 1:4], rtol=2e-3, atol=1e-5)
+
+
+@pytest.mark.parametrize("H,W,K,M,sp,T", [
+    (1021, 1999, 16, 1, 1, 60),       # prime row length: Bluestein transform of 4000-odd points
+    (1499, 2047, 8, 1, 2, 60),        # 2047 = 23 * 89: direct prime stages
+    (768, 1024, 32, 1, np.inf, 60),   # K = 32 (one class per lane of a warp)
+    (2048, 2048, 16, 2, 1, 20),       # the 5x5 patch on the 2048 x 2048 scene
+    (512, 700, 16, 3, 1, 20)])        # a 7x7 patch (three-launch sweep) on a large image
+def test_large_shapes_against_fp64(B, H, W, K, M, sp, T):
+    """Large and odd shapes outside the five workloads: the FP32 handle against the FP64
+    handle (itself held to the oracle at 1e-9 by the parity tests), z within 1e-4 and labels
+    equal off the 1e-3 margin band."""
+    sc = synth.scene(H, W, K, S=24, gap=2.0, noise_std=1.0, wrong_frac=0.05, seed=H + W)
+    z = {}
+    for prec, dt in (("fp32", np.float32), ("fp64", np.float64)):
+        s = B.Solver(B.make_params(H, W, K, M=M, sigma=max(0.5, 0.5 * M), lam=1.5, mu=1.0,
+                                   schatten_p=sp, precision=prec))
+        s.set_probs(sc.p.astype(dt))
+        s.solve(T, trace_every=10)
+        z[prec] = s.get_z()
+        s.close()
+    assert np.isfinite(z["fp32"]).all()
+    assert max_abs(z["fp32"], z["fp64"]) < 1e-4
+    ok, _ = label_agreement(z["fp32"], z["fp64"])
+    assert ok
