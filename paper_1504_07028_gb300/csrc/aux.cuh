@@ -54,6 +54,25 @@ __global__ void k_hwk_to_khw(const T* src, T* dst, int n, int K) {
   dst[i] = src[pix * K + k];
 }
 
+// The full form of the local duals ([n][3][K]: d1, d3, d4) from the compact form the affine
+// sweep writes ([n][K + 2]: d3, c1, c4; d1 = c1 p, d4 = c4 1), with the sweep's own product
+// for d1, so that either form gives the next sweep the same values.
+template <typename T>
+__global__ void k_dl_expand(const T* __restrict__ dc, const T* __restrict__ p, T* __restrict__ dl,
+                            int n, int K) {
+  const size_t tot = (size_t)n * K;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / K;
+    const int k = (int)(i - pix * K);
+    const T* c = dc + pix * (K + 2);
+    T* o = dl + pix * 3 * K + k;
+    o[0] = c[K] * p[i];
+    o[K] = c[k];
+    o[2 * K] = c[K + 1];
+  }
+}
+
 // argmax_k z_k, ties to the lowest k.
 template <typename T>
 __global__ void k_labels(const T* z, int n, int K, int32_t* lab) {

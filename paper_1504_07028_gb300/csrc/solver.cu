@@ -421,6 +421,7 @@ struct Carver {
 template <typename T>
 struct Buffers {
   T *p, *z, *dloc, *d2, *P, *P2, *zp, *tmp, *rhsd;
+  T* dcmp;  // compact local duals [n][K + 2] (d3, c1, c4) of the affine fused sweep
   T* wbuf;  // wide patches: scratch [n][L][K][2] (the old d2 of a traced sweep; checkpoint read-out)
   T* coef;  // wide patches: [n][4] the 2 x 2 prox matrix A of the last sweep (d2 = V (A - I))
   cplx<T>* S;
@@ -444,6 +445,7 @@ static size_t carve(const Plan& pl, char* base, Buffers<T>& b) {
   b.p = c.take<T>(nK + 64 / sizeof(T));
   b.z = c.take<T>(nK);
   b.dloc = c.take<T>(3 * nK + 64 / sizeof(T));
+  b.dcmp = c.take<T>((size_t)pl.n * (pl.K + 2) + 64 / sizeof(T));
   b.d2 = c.take<T>(2 * (size_t)pl.L * nK + 64 / sizeof(T));
   const size_t tslot = (size_t)pl.ntiles * pl.EHmax * pl.EWmax * pl.K;
   b.P = c.take<T>(tslot);
@@ -498,6 +500,13 @@ class Solver : public SolverBase {
   int iter = 0;
   bool have_probs = false;
   bool rhs_dense = false;  // next z-update reads b.rhsd instead of the partials
+  // the local duals are held in compact form (b.dcmp, written by the affine fused sweep)
+  // rather than in full form (b.dloc: set_probs, set_state, the simplex and wide sweeps)
+  bool dl_cmp = false;
+
+  // The form of the local duals the handle's sweeps keep from iteration to iteration (graphs
+  // are captured in it): compact for the affine fused sweep, full otherwise.
+  bool dl_steady() const { return pl.wide || (g4 == SEGSALSA_G4_SIMPLEX ? !dl_cmp : dl_cmp); }
   int64_t nlaunch[NKIND] = {0};
   double ms[NKIND] = {0};
   bool profiling = false;
@@ -703,6 +712,16 @@ class Solver : public SolverBase {
     return a;
   }
 
+  // Bring the full form up to date (d1 = c1 p, d4 = c4 1) and make it the one in use.
+  int dl_to_full() {
+    if (!dl_cmp) return SEGSALSA_OK;
+    const size_t nK = (size_t)pl.n * pl.K;
+    const int blocks = (int)std::min<size_t>((nK + AUX_THREADS - 1) / AUX_THREADS, 152 * 8);
+    SGS_LAUNCH(KIND_OTHER, (k_dl_expand<T><<<blocks, AUX_THREADS, 0, st>>>(b.dcmp, b.p, b.dloc, pl.n, pl.K)));
+    dl_cmp = false;
+    return SEGSALSA_OK;
+  }
+
   // z = (3 I + J^T J)^{-1} rhs; rhs dense (src) or the sweep's rhs (src == nullptr: the tile
   // partials, or the dense rhs of the wide-patch sweep)
   int z_update(const T* src, T* zout) {
@@ -763,7 +782,9 @@ class Solver : public SolverBase {
   }
 
   int sweep(bool diag) {
+    int rc;
     if (pl.wide) {
+      if ((rc = dl_to_full())) return rc;     // the wide kernels keep the full form
       WideArgs<T> w{};
       w.H = pl.H; w.W = pl.W; w.K = pl.K; w.M = pl.M; w.L = pl.L;
       w.z = b.z; w.p = b.p; w.dloc = b.dloc; w.V = b.d2; w.coef = b.coef; w.scratch = b.wbuf;
@@ -778,10 +799,16 @@ class Solver : public SolverBase {
       }));
       return SEGSALSA_OK;
     }
+    const bool simplex = g4 == SEGSALSA_G4_SIMPLEX;
+    // the simplex sweep reads and writes the full form of the local duals; the affine sweep
+    // reads either form and writes the compact one
+    if (simplex && (rc = dl_to_full())) return rc;
     SweepArgs<T> a{};
     a.H = pl.H; a.W = pl.W; a.K = pl.K; a.NC = pl.NC; a.ntx = pl.ntx; a.nty = pl.nty;
     a.EHmax = pl.EHmax; a.EWmax = pl.EWmax;
     a.z = b.z; a.p = b.p; a.dloc = b.dloc; a.d2 = b.d2; a.P = b.P; a.P2 = b.P2;
+    a.dcmp = b.dcmp;
+    a.cin = (!simplex && dl_cmp) ? 1 : 0;
     a.diag_sq = b.dsq; a.omega = b.omega;
     a.tau = (T)(lambda / mu); a.mu = (T)mu; a.invK = (T)(1.0 / pl.K); a.sp = sp;
     a.err = b.err;
@@ -789,10 +816,11 @@ class Solver : public SolverBase {
     a.probe = wait_probe ? 16u : 0u;
     const size_t smem = diag ? pl.sweep_smem_diag : pl.sweep_smem;
     SGS_CUDA(launch(KIND_SWEEP, [&]() {
-      if (g4 == SEGSALSA_G4_SIMPLEX) return launch_sweep_simplex<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
+      if (simplex) return launch_sweep_simplex<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
       return pl.K == pl.G && pl.NC == 256 / pl.G ? launch_sweep_keq<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st)
                           : launch_sweep<T>(a, pl.M, pl.G, diag, pl.ntiles, smem, st);
     }));
+    if (!simplex) dl_cmp = true;
     return SEGSALSA_OK;
   }
 
@@ -845,6 +873,7 @@ class Solver : public SolverBase {
     SGS_CUDA(cudaMemcpyAsync(b.p, b.tmp, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st));
     SGS_LAUNCH(KIND_OTHER, (k_init_z<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.p, b.z, n, K)));
     SGS_CUDA(cudaMemsetAsync(b.dloc, 0, sizeof(T) * 3 * nK, st));
+    dl_cmp = false;
     SGS_CUDA(cudaMemsetAsync(b.d2, 0, sizeof(T) * 2 * pl.L * nK, st));
     if (pl.wide) SGS_CUDA(cudaMemsetAsync(b.coef, 0, sizeof(T) * 4 * (size_t)n, st));  // V = 0: d2 = 0
     SGS_CUDA(cudaStreamSynchronize(st));
@@ -991,7 +1020,9 @@ class Solver : public SolverBase {
     while (it < iters) {
       const int left = iters - it;
       // a whole traced period (or an untraced block) that ends before or at the last iteration
-      const bool can_graph = use_graphs && !profiling && iter >= 1 && !rhs_dense;
+      // (graphs are captured with the local duals in their steady form: after set_probs,
+      // set_state or a switch of g4 the first iteration runs eagerly)
+      const bool can_graph = use_graphs && !profiling && iter >= 1 && !rhs_dense && dl_steady();
       int len = 0;
       if (can_graph) {
         if (trace) {
@@ -1081,6 +1112,7 @@ class Solver : public SolverBase {
     if (!have_probs) return fail(SEGSALSA_ERR_STATE, "no state: call set_probs first");
     const size_t nK = (size_t)pl.n * pl.K;
     int rc;
+    if ((d1 || d3 || d4) && (rc = dl_to_full())) return rc;   // d1, d3, d4 from the full form
     if (z && (rc = copy_out(z, b.z, nK, dev))) return rc;
     if (d2 && pl.wide) {
       // the wide sweep stores d2 as (V, A): d2 = V (A - I)
@@ -1122,6 +1154,7 @@ class Solver : public SolverBase {
     int rc;
     if ((rc = copy_in(b.z, z, nK, dev))) return rc;
     if ((rc = copy_in(b.d2, d2, 2 * pl.L * nK, dev))) return rc;
+    dl_cmp = false;                 // d1, d3, d4 arrive in full form
     if (pl.wide) SGS_CUDA(launch_wide_coef_identity<T>(b.coef, pl.n, st));  // V = d2, A = 2I
     const void* dl[3] = {d1, d3, d4};
     for (int j = 0; j < 3; ++j) {
@@ -1205,7 +1238,7 @@ class Solver : public SolverBase {
 
   // ------------------------------------------------------------------ batch support
   bool ready() const override { return have_probs; }
-  bool graphable() const override { return have_probs && iter >= 1 && !rhs_dense; }
+  bool graphable() const override { return have_probs && iter >= 1 && !rhs_dense && dl_steady(); }
   int enqueue_iterations(int len, cudaStream_t s) override {
     cudaStream_t keep = st;
     const bool keep_prof = profiling;
@@ -1365,6 +1398,7 @@ class Solver : public SolverBase {
     plan(cm, ck, fin, zs, dls, d2s, vbl, vb2, zb, bb, glp, part, acc);
     auto save = [&](T* dst) -> cudaError_t {
       cudaError_t r;
+      if (dl_to_full()) return cudaErrorUnknown;   // checkpoints hold the full form
       if ((r = cudaMemcpyAsync(dst, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st))) return r;
       if ((r = cudaMemcpyAsync(dst + nK, b.dloc, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st))) return r;
       if ((r = cudaMemcpyAsync(dst + nK + nloc, b.d2, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st))) return r;
@@ -1374,6 +1408,7 @@ class Solver : public SolverBase {
       cudaError_t r;
       if ((r = cudaMemcpyAsync(b.z, src, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st))) return r;
       if ((r = cudaMemcpyAsync(b.dloc, src + nK, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st))) return r;
+      dl_cmp = false;
       if ((r = cudaMemcpyAsync(b.d2, src + nK + nloc, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st))) return r;
       return cudaMemcpyAsync(b.P, src + nK + nloc + n2, sizeof(T) * tslot, cudaMemcpyDeviceToDevice, st);
     };
@@ -1381,6 +1416,7 @@ class Solver : public SolverBase {
     // forward from z^0 = p / 1^T p, d^0 = 0, with a checkpoint every `every` iterations
     SGS_LAUNCH(KIND_OTHER, (k_init_z<T><<<grid1(n), AUX_THREADS, 0, st>>>(b.p, b.z, n, K)));
     SGS_CUDA(cudaMemsetAsync(b.dloc, 0, sizeof(T) * nloc, st));
+    dl_cmp = false;
     SGS_CUDA(cudaMemsetAsync(b.d2, 0, sizeof(T) * n2, st));
     iter = 0;
     rhs_dense = false;
@@ -1412,6 +1448,7 @@ class Solver : public SolverBase {
       for (int k = k0; k <= k1; ++k) {
         const int i = k - k0;
         SGS_CUDA(cudaMemcpyAsync(zs + (size_t)i * nK, b.z, sizeof(T) * nK, cudaMemcpyDeviceToDevice, st));
+        if ((rc = dl_to_full())) return rc;           // the reverse units read the full form
         SGS_CUDA(cudaMemcpyAsync(dls + (size_t)i * nloc, b.dloc, sizeof(T) * nloc, cudaMemcpyDeviceToDevice, st));
         SGS_CUDA(cudaMemcpyAsync(d2s + (size_t)i * n2, b.d2, sizeof(T) * n2, cudaMemcpyDeviceToDevice, st));
         if (k < k1) {
@@ -1481,8 +1518,14 @@ class Solver : public SolverBase {
 
   int traffic(double* sw, double* it) const override {
     const double unit = (double)sizeof(T) * pl.n * pl.K;
-    if (sw) *sw = unit * (4.0 * pl.L + 9.0);
-    if (it) *it = unit * (4.0 * pl.L + 11.0);
+    // per pixel and class: d2 read and written (4L values), z, p, rhs (3), d3 read and written
+    // (2), and d1, d4 either per class (4 more: the simplex and wide sweeps) or as the two
+    // per-pixel scalars of the compact form, read and written (4 per pixel: the affine sweep)
+    const bool compact = !pl.wide && g4 != SEGSALSA_G4_SIMPLEX;
+    const double s = compact ? unit * (4.0 * pl.L + 5.0) + 4.0 * sizeof(T) * pl.n
+                             : unit * (4.0 * pl.L + 9.0);
+    if (sw) *sw = s;
+    if (it) *it = s + 2.0 * unit;
     return SEGSALSA_OK;
   }
 };

@@ -34,7 +34,10 @@ struct SweepArgs {
   int EHmax, EWmax;      // extents of the P tile slots (tile + halo), in pixels
   const T* z;            // [n][K]
   const T* p;            // [n][K]
-  T* dloc;               // [n][3][K]  (d1, d3, d4)
+  T* dloc;               // [n][3][K]  (d1, d3, d4): full form of the local duals
+  T* dcmp;               // [n][K + 2] (d3, c1, c4): compact form, d1 = c1 p, d4 = c4 1 (affine g4)
+  int cin;               // affine g4: the local duals come in compact form (else full form);
+                         // the affine sweep writes the compact form, the simplex sweep the full
   T* d2;                 // [n][L][K][2]
   T* P;                  // [tiles][EHmax][EWmax][K]  partial sums of G^T(u + d)
   T* P2;                 // DIAG: partial sums of G^T d (dual residual)
@@ -129,11 +132,12 @@ __device__ __forceinline__ void issue_row(const SweepArgs<T>& a, size_t pix0, in
                                           unsigned char* st, size_t d2b, size_t dlb,
                                           uint64_t* bar, uint32_t extra = 0) {
   const int K = a.K;
+  const int dls = a.cin ? K + 2 : 3 * K;   // local-dual values per pixel in the input form
   const char* g0 = reinterpret_cast<const char*>(a.d2) + pix0 * (2 * L * K * sizeof(T));
-  const char* g1 = reinterpret_cast<const char*>(a.dloc) + pix0 * (3 * K * sizeof(T));
+  const char* g1 = reinterpret_cast<const char*>(a.cin ? a.dcmp : a.dloc) + pix0 * (dls * sizeof(T));
   const char* g2 = reinterpret_cast<const char*>(a.p) + pix0 * (K * sizeof(T));
   const size_t n0 = (size_t)TW * 2 * L * K * sizeof(T);
-  const size_t n1 = (size_t)TW * 3 * K * sizeof(T);
+  const size_t n1 = (size_t)TW * dls * sizeof(T);
   const size_t n2 = (size_t)TW * K * sizeof(T);
   const char* a0 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g0) & ~uintptr_t(15));
   const char* a1 = reinterpret_cast<const char*>(reinterpret_cast<uintptr_t>(g1) & ~uintptr_t(15));
@@ -314,10 +318,12 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     unsigned char* st = stage0 + sidx * stb;
     // the consumer's view of the three regions (same 16-byte rounding as issue_row)
     const uintptr_t q0 = reinterpret_cast<uintptr_t>(a.d2) + pix0 * (2 * L * K * sizeof(T));
-    const uintptr_t q1 = reinterpret_cast<uintptr_t>(a.dloc) + pix0 * (3 * K * sizeof(T));
+    const bool cin = !SIMP && a.cin;      // the simplex sweep always reads the full form
+    const int dls = cin ? K + 2 : 3 * K;
+    const uintptr_t q1 = reinterpret_cast<uintptr_t>(cin ? a.dcmp : a.dloc) + pix0 * (dls * sizeof(T));
     const uintptr_t q2 = reinterpret_cast<uintptr_t>(a.p) + pix0 * (K * sizeof(T));
     const V2* sd2 = reinterpret_cast<const V2*>(st + (q0 & 15)) + (size_t)c * L * K + g;
-    const T* sdl = reinterpret_cast<const T*>(st + d2b + (q1 & 15)) + (size_t)c * 3 * K + g;
+    const T* sdp = reinterpret_cast<const T*>(st + d2b + (q1 & 15)) + (size_t)c * dls;  // pixel
     const T* sp = reinterpret_cast<const T*>(st + d2b + dlb + (q2 & 15)) + (size_t)c * K + g;
     // ---- loads: duals and p of this pixel / class (from the staged row)
     V2 dv[L];
@@ -329,9 +335,15 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     T pk = T(0), d1 = T(0), d3 = T(0), d4 = T(0);
     if (kok) {
       pk = sp[0];
-      d1 = sdl[0];
-      d3 = sdl[K];
-      d4 = sdl[2 * K];
+      if (cin) {            // d1 = c1 p, d4 = c4 1 (the forms the MPOs of g1 and g4 leave)
+        d3 = sdp[g];
+        d1 = sdp[K] * pk;
+        d4 = sdp[K + 1];
+      } else {
+        d1 = sdp[g];
+        d3 = sdp[K + g];
+        d4 = sdp[2 * K + g];
+      }
     }
     // ---- v2 = J z - d2 (eq. 4), from the shared tile
     const T* zc = zs + ((r + M) * EWs + (c + M)) * G + g;
@@ -400,11 +412,16 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
     const T q = T(4) * pp / mu;
     const T disc = sqrt(pv * pv + q);
     const T sroot = (pv >= T(0)) ? T(0.5) * (pv + disc) : (T(0.5) * q) / (disc - pv);
-    const T u1 = v1 + pk / (mu * sroot);
+    // the new d1 is p / (mu sroot) = c1 p and, for the affine g4, the new d4 is the same
+    // -(1^T v4 - 1) / K for every class: the compact form stores c1 and c4 per pixel
+    const T c1n = T(1) / (mu * sroot);
+    const T u1 = SIMP ? v1 + pk / (mu * sroot) : v1 + pk * c1n;
     const T u3 = fmax(v3, T(0));
     T u4;
+    T c4n = T(0);
     if constexpr (!SIMP) {
-      u4 = v4 - (s4 - T(1)) * a.invK;
+      c4n = -(s4 - T(1)) * a.invK;
+      u4 = v4 + c4n;
     } else {
       // Michelot: threshold over the active classes until no class leaves the active set (at
       // most K passes; the loop runs until no group of the warp changes, so that every lane
@@ -423,12 +440,23 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<T, M, DIAG>()) k_sweep(c
       }
       u4 = kok ? fmax(v4 - theta, T(0)) : T(0);
     }
-    const T n1 = u1 - v1, n3 = u3 - v3, n4 = u4 - v4;
+    const T n1 = SIMP ? u1 - v1 : pk * c1n, n3 = u3 - v3, n4 = SIMP ? u4 - v4 : c4n;
+    if constexpr (SIMP) {
+      if (kok) {
+        T* dl = a.dloc + pix * 3 * K + g;
+        dl[0] = n1;
+        dl[K] = n3;
+        dl[2 * K] = n4;
+      }
+    } else {
+      T* dc = a.dcmp + pix * (K + 2);
+      if (kok) dc[g] = n3;
+      if (kok && g == 0) {
+        dc[K] = c1n;
+        dc[K + 1] = c4n;
+      }
+    }
     if (kok) {
-      T* dl = a.dloc + pix * 3 * K + g;
-      dl[0] = n1;
-      dl[K] = n3;
-      dl[2 * K] = n4;
       accW[M][M] += (u1 + n1) + (u3 + n3) + (u4 + n4);
       if constexpr (DIAG) {
         accW2[M][M] += n1 + n3 + n4;

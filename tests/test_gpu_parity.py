@@ -371,3 +371,34 @@ def test_graph_replay_matches_eager_launches(B):
     assert np.array_equal(t0, t1)
     assert np.array_equal(z0, z1)
     assert list(t0[:, 0]) == [10, 20, 30, 40, 47]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_compact_local_duals_are_transparent(B, prec):
+    """The affine sweep keeps d1 = c1 p and d4 = c4 1 as two scalars per pixel (the forms the
+    MPOs of g1 and g4 leave); get_state expands them. Reading the state in the middle of a solve
+    (which switches the handle to the full form for one sweep) must not change the iterates by a
+    bit, and the expanded duals must be the oracle's."""
+    H, W, K, M = 33, 41, 6, 1
+    sc = synth.scene(H, W, K, S=5, gap=2.0, noise_std=1.0, wrong_frac=0.05, seed=97)
+    dt = np.float64 if prec == "fp64" else np.float32
+    p = sc.p.astype(dt)
+    a = _solver(B, H, W, K, M, 0.5, 1.5, 1.0, 1, prec)
+    b = _solver(B, H, W, K, M, 0.5, 1.5, 1.0, 1, prec)
+    a.set_probs(p)
+    b.set_probs(p)
+    a.solve(40, trace_every=10)
+    b.solve(17, trace_every=10)
+    g = b.get_state()                       # mid-solve: the duals leave the compact form
+    b.solve(23, trace_every=10)
+    assert np.array_equal(a.get_z(), b.get_z())
+    assert np.array_equal(a.get_state()["d1"], b.get_state()["d1"])
+    st, _ = O.solve(p.astype(np.float64), M, 0.5, 1.5, 1.0, 1, 17)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert max_abs(hwk_to_khw(g["d1"]), st.d[0]) <= tol
+    assert max_abs(hwk_to_khw(g["d3"]), st.d[2]) <= tol
+    assert max_abs(hwk_to_khw(g["d4"]), st.d[3]) <= tol
+    # d4 is the same for every class of a pixel, d1 is parallel to p
+    assert np.array_equal(g["d4"], np.repeat(g["d4"][..., :1], K, axis=-1))
+    a.close()
+    b.close()
