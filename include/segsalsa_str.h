@@ -273,7 +273,10 @@ int segsalsa_str_kernel_stats(segsalsa_str_t* h, int64_t* launches, double* ms);
 int segsalsa_str_reset_stats(segsalsa_str_t* h);
 
 /* Algorithmic device bytes moved by one fused-sweep launch and one full iteration (the
- * minimum traffic model: every array read or written once, no halo or pass overhead). */
+ * minimum traffic model: every array read or written once, no halo or pass overhead). With
+ * the affine g4 and patches up to 5x5 the sweep keeps d1 and d4 as one scalar per pixel each
+ * (d1 = c1 p, d4 = c4 1, the forms the MPOs of g1 and g4 leave), so the model counts K + 2
+ * local-dual values per pixel; with the simplex g4 or 7x7 ... 11x11 patches it counts 3K. */
 int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
                                double* iteration_bytes);
 
