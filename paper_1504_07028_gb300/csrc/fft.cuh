@@ -1388,12 +1388,28 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const 
         p2_load_block<T, 1>(a.src + ((size_t)y * N + t + r * NB) * a.K + cq, c);
         v[r] = c[0];
       }
+    } else if (!hy) {
+      // a row with one vertical cover (most rows): p00 (+ p01) for all eight pixels, every
+      // load issued before any sum, so that one memory latency covers the whole butterfly
+      C c0[8], c1[8];
+      bool hx[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int2 ox = __ldg(reinterpret_cast<const int2*>(a.offX) + t + r * NB);
+        hx[r] = ox.y >= 0;
+        const int o1 = hx[r] ? ox.y : ox.x;
+        C e[1];
+        p2_load_block<T, 1>(a.P + rb0 + ox.x + cq, e); c0[r] = e[0];
+        p2_load_block<T, 1>(a.P + rb0 + o1 + cq, e);   c1[r] = e[0];
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = hx[r] ? cadd(c0[r], c1[r]) : c0[r];
     } else {
       // p00 (+ p01) (+ p10) (+ p11), the order of gather_row16. All loads of the butterfly
       // are issued before any sum (an absent cover aliases the first, its value is dropped),
       // so that they are in flight together.
-      // (in two batches of four pixels, to keep the registers of three CTAs per SM)
-      const int rb1a = hy ? rb1 : rb0;
+      // (in two batches of four pixels, within the register budget of a 1024-thread CTA)
+      const int rb1a = rb1;
 #pragma unroll
       for (int h = 0; h < 8; h += 4) {
         C c00[4], c01[4], c10[4], c11[4];
