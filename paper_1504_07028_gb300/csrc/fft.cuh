@@ -1253,12 +1253,13 @@ struct P2Plan {
 
 // One Stockham stage of radix R with Ns = NS on B interleaved sequences (generic fft_stage
 // with compile-time arguments).
-template <typename T, int N, int B, int R, int NS>
+template <typename T, int N, int B, int R, int NS, int TH>
 __device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T>* __restrict__ Xout,
                                          const cplx<T>* tw) {
   using C = cplx<T>;
   constexpr int NB = N / R;
   constexpr int ITEMS = NB * B;
+  static_assert(ITEMS % TH == 0, "whole butterflies per thread");
   constexpr int STRIDE = NB / NS;
   // a butterfly's R inputs (outputs) are NB * B (NS * B) elements apart: where that is a whole
   // number of pad periods, the padded slots differ by a constant, so one padded base address
@@ -1266,7 +1267,10 @@ __device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T
   constexpr int PP = 1 << PadShift<T>::v;
   constexpr bool IN_CONST = (NB * B) % PP == 0, OUT_CONST = (NS * B) % PP == 0;
   constexpr int SI = NB * B + NB * B / PP, SO = NS * B + NS * B / PP;
-  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+  // the CTA has TH threads: ITEMS / TH butterflies each, unrolled so that their loads overlap
+#pragma unroll
+  for (int u = 0; u < ITEMS / TH; ++u) {
+    const int it = threadIdx.x + u * TH;
     const int t = it / B, b = it - t * B;
     const int g = t / NS;
     const int j = t - g * NS;
@@ -1312,25 +1316,28 @@ __device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T
 }
 
 // The stages after the first (Ns = NS onwards), ping-ponging; returns the result buffer.
-template <typename T, int N, int B, int NS>
+template <typename T, int N, int B, int NS, int TH>
 __device__ __forceinline__ cplx<T>* p2_rest(cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
   if constexpr (NS == N) {
     return in;
   } else {
     constexpr int R = (N / NS >= 8) ? 8 : (N / NS == 4 ? 4 : 2);
-    p2_stage<T, N, B, R, NS>(in, out, tw);
+    p2_stage<T, N, B, R, NS, TH>(in, out, tw);
     __syncthreads();
-    return p2_rest<T, N, B, NS * R>(out, in, tw);
+    return p2_rest<T, N, B, NS * R, TH>(out, in, tw);
   }
 }
 
 // First stage (radix 8, Ns = 1, no twiddles) of sequence b of butterfly t from registers.
+// With B <= 4 the residue of base = 8 B t + b modulo the pad period is at most b (or 8 for
+// FP32, B = 1), so output r lies (r B) >> PadShift pad slots past base's: fixed offsets.
 template <typename T, int N, int B>
 __device__ __forceinline__ void p2_first(cplx<T> (&v)[8], int t, int b, cplx<T>* Xout) {
+  static_assert(B == 1 || B == 2 || B == 4, "class pairs per CTA");
   Dft<8, cplx<T>>::run(v);
-  const int base = t * 8 * B + b;
+  cplx<T>* xo = Xout + px<T>(t * 8 * B + b);
 #pragma unroll
-  for (int r = 0; r < 8; ++r) Xout[px<T>(base + r * B)] = v[r];
+  for (int r = 0; r < 8; ++r) xo[r * B + ((r * B) >> PadShift<T>::v)] = v[r];
 }
 
 // 2B consecutive values of type T (one class block of a pixel) as complex pairs.
@@ -1357,7 +1364,7 @@ __device__ __forceinline__ void p2_load_block(const T* __restrict__ src, cplx<T>
 
 // Threads of a power-of-two row CTA: one first-stage butterfly of one sequence each.
 template <int LOGN, int B>
-constexpr int p2_threads() {
+__host__ __device__ constexpr int p2_threads() {
   return ((1 << LOGN) / 8 * B) > 1024 ? 1024 : ((1 << LOGN) / 8 * B);
 }
 
@@ -1438,7 +1445,7 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const 
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8>(Y, X, tw);
+  const C* R = p2_rest<T, N, B, 8, p2_threads<LOGN, B>()>(Y, X, tw);
   pdl_trigger();
   // unpack the two real spectra of each pair (as k_row_forward)
   for (int i = threadIdx.x; i < (N / 2 + 1) * B; i += blockDim.x) {
@@ -1466,23 +1473,26 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_inverse_p2(const 
   const int q0 = blockIdx.x * B;
   const C* tw = a.pl.tw;
   pdl_wait();  // the spectrum comes from the column pass
+  const C* srow = a.S + (size_t)y * WH * a.K + 2 * q0;
   for (int it = threadIdx.x; it < NB * B; it += blockDim.x) {
     const int t = it / B, q = it - t * B;
     C v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int kx = t + r * NB;
-      const int ks = kx < WH ? kx : N - kx;
+      // bin kx = t + r N/8 of the full spectrum: stored for r < 4 (kx < N/2) and at kx = N/2
+      // (r = 4, t = 0); the Hermitian mirror ks = N - kx (conjugated) for r > 4 and r = 4, t > 0
+      const int ks = r < 4 ? t + r * NB : (r == 4 ? N / 2 - t : N - t - r * NB);
+      const bool cj = r > 4 || (r == 4 && t > 0);
       C A, Bq;
-      load_pair(a.S + ((size_t)y * WH + ks) * a.K + 2 * (q0 + q), A, Bq);
-      if (kx >= WH) { A = cconj(A); Bq = cconj(Bq); }
+      load_pair(srow + (size_t)ks * a.K + 2 * q, A, Bq);
+      if (cj) { A = cconj(A); Bq = cconj(Bq); }
       C xv; xv.x = A.x - Bq.y; xv.y = -(A.y + Bq.x);   // conj(A + i B)
       v[r] = xv;
     }
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8>(Y, X, tw);
+  const C* R = p2_rest<T, N, B, 8, p2_threads<LOGN, B>()>(Y, X, tw);
   pdl_trigger();
   const T inv = T(1) / T(N);
   constexpr int VE = 16 / sizeof(T);
