@@ -1251,80 +1251,110 @@ struct P2Plan {
   static constexpr int N = 1 << LOGN;
 };
 
-// One Stockham stage of radix R with Ns = NS on B interleaved sequences (generic fft_stage
-// with compile-time arguments).
-template <typename T, int N, int B, int R, int NS, int TH>
-__device__ __forceinline__ void p2_stage(const cplx<T>* __restrict__ Xin, cplx<T>* __restrict__ Xout,
-                                         const cplx<T>* tw) {
+// Butterfly it of a compile-time Stockham stage (radix R, Ns = NS, B interleaved sequences):
+// p2_load reads its R inputs, p2_butterfly twiddles, transforms and writes them. A butterfly's
+// R inputs (outputs) are NB * B (NS * B) elements apart: where that is a whole number of pad
+// periods, the padded slots differ by a constant, so one padded base address and immediate
+// offsets replace R index computations (same slots, same results).
+template <typename T, int N, int B, int R>
+__device__ __forceinline__ void p2_load(const cplx<T>* __restrict__ Xin, int it, cplx<T> (&v)[R]) {
+  constexpr int NB = N / R;
+  constexpr int PP = 1 << PadShift<T>::v;
+  const int t = it / B, b = it - t * B;
+  if constexpr ((NB * B) % PP == 0) {
+    constexpr int SI = NB * B + NB * B / PP;
+    const cplx<T>* xi = Xin + px<T>(t * B + b);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = xi[r * SI];
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * NB) * B + b)];
+  }
+}
+template <typename T, int N, int B, int R, int NS>
+__device__ __forceinline__ void p2_butterfly(cplx<T>* __restrict__ Xout, int it, cplx<T> (&v)[R],
+                                             const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int NB = N / R;
-  constexpr int ITEMS = NB * B;
-  static_assert(ITEMS % TH == 0, "whole butterflies per thread");
   constexpr int STRIDE = NB / NS;
-  // a butterfly's R inputs (outputs) are NB * B (NS * B) elements apart: where that is a whole
-  // number of pad periods, the padded slots differ by a constant, so one padded base address
-  // and immediate offsets replace R index computations (same slots, same results)
   constexpr int PP = 1 << PadShift<T>::v;
-  constexpr bool IN_CONST = (NB * B) % PP == 0, OUT_CONST = (NS * B) % PP == 0;
-  constexpr int SI = NB * B + NB * B / PP, SO = NS * B + NS * B / PP;
-  // the CTA has TH threads: ITEMS / TH butterflies each, unrolled so that their loads overlap
-#pragma unroll
-  for (int u = 0; u < ITEMS / TH; ++u) {
-    const int it = threadIdx.x + u * TH;
-    const int t = it / B, b = it - t * B;
-    const int g = t / NS;
-    const int j = t - g * NS;
-    C v[R];
-    if constexpr (IN_CONST) {
-      const C* xi = Xin + px<T>(t * B + b);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = xi[r * SI];
-    } else {
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = Xin[px<T>((t + r * NB) * B + b)];
-    }
-    if constexpr (NS > 1) {
-      const C w1 = tw[j * STRIDE];
-      v[1] = cmul(v[1], w1);
-      if constexpr (R > 2) {
-        const C w2 = cmul(w1, w1);
-        v[2] = cmul(v[2], w2);
-        if constexpr (R > 3) {
-          const C w3 = cmul(w2, w1);
-          v[3] = cmul(v[3], w3);
-          if constexpr (R > 4) {
-            const C w4 = tw[4 * j * STRIDE];
-            v[4] = cmul(v[4], w4);
-            v[5] = cmul(v[5], cmul(w4, w1));
-            v[6] = cmul(v[6], cmul(w4, w2));
-            v[7] = cmul(v[7], cmul(w4, w3));
-          }
+  const int t = it / B, b = it - t * B;
+  const int g = t / NS;
+  const int j = t - g * NS;
+  if constexpr (NS > 1) {
+    const C w1 = tw[j * STRIDE];
+    v[1] = cmul(v[1], w1);
+    if constexpr (R > 2) {
+      const C w2 = cmul(w1, w1);
+      v[2] = cmul(v[2], w2);
+      if constexpr (R > 3) {
+        const C w3 = cmul(w2, w1);
+        v[3] = cmul(v[3], w3);
+        if constexpr (R > 4) {
+          const C w4 = tw[4 * j * STRIDE];
+          v[4] = cmul(v[4], w4);
+          v[5] = cmul(v[5], cmul(w4, w1));
+          v[6] = cmul(v[6], cmul(w4, w2));
+          v[7] = cmul(v[7], cmul(w4, w3));
         }
       }
     }
-    Dft<R, C>::run(v);
-    const int base = (g * NS * R + j) * B + b;
-    if constexpr (OUT_CONST) {
-      C* xo = Xout + px<T>(base);
+  }
+  Dft<R, C>::run(v);
+  const int base = (g * NS * R + j) * B + b;
+  if constexpr ((NS * B) % PP == 0) {
+    constexpr int SO = NS * B + NS * B / PP;
+    C* xo = Xout + px<T>(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) xo[r * SO] = v[r];
-    } else {
+    for (int r = 0; r < R; ++r) xo[r * SO] = v[r];
+  } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) Xout[px<T>(base + r * NS * B)] = v[r];
-    }
+    for (int r = 0; r < R; ++r) Xout[px<T>(base + r * NS * B)] = v[r];
   }
 }
 
-// The stages after the first (Ns = NS onwards), ping-ponging; returns the result buffer.
-template <typename T, int N, int B, int NS, int TH>
+// One Stockham stage (generic fft_stage with compile-time arguments) on a CTA of TH threads,
+// ITEMS / TH butterflies a thread, unrolled. Two buffers: each butterfly is read and written in
+// turn. ONE (in place, Xout == Xin): every thread reads the inputs of all its butterflies, the
+// CTA synchronises, then they are transformed and written.
+template <typename T, int N, int B, int R, int NS, int TH, bool ONE>
+__device__ __forceinline__ void p2_stage(const cplx<T>* Xin, cplx<T>* Xout, const cplx<T>* tw) {
+  constexpr int ITEMS = N / R * B;
+  static_assert(ITEMS % TH == 0, "whole butterflies per thread");
+  constexpr int IPT = ITEMS / TH;
+  if constexpr (ONE) {
+    cplx<T> v[IPT][R];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) p2_load<T, N, B, R>(Xin, threadIdx.x + u * TH, v[u]);
+    __syncthreads();  // every input read before any output lands on it
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) p2_butterfly<T, N, B, R, NS>(Xout, threadIdx.x + u * TH, v[u], tw);
+  } else {
+    cplx<T> v[IPT][R];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) p2_load<T, N, B, R>(Xin, threadIdx.x + u * TH, v[u]);
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) p2_butterfly<T, N, B, R, NS>(Xout, threadIdx.x + u * TH, v[u], tw);
+  }
+}
+
+// The stages after the first (Ns = NS onwards), ping-ponging between two buffers, or in place
+// in one (ONE); returns the result buffer.
+template <typename T, int N, int B, int NS, int TH, bool ONE>
 __device__ __forceinline__ cplx<T>* p2_rest(cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
   if constexpr (NS == N) {
     return in;
   } else {
     constexpr int R = (N / NS >= 8) ? 8 : (N / NS == 4 ? 4 : 2);
-    p2_stage<T, N, B, R, NS, TH>(in, out, tw);
-    __syncthreads();
-    return p2_rest<T, N, B, NS * R, TH>(out, in, tw);
+    if constexpr (ONE) {
+      p2_stage<T, N, B, R, NS, TH, true>(in, in, tw);
+      __syncthreads();
+      return p2_rest<T, N, B, NS * R, TH, true>(in, in, tw);
+    } else {
+      p2_stage<T, N, B, R, NS, TH, false>(in, out, tw);
+      __syncthreads();
+      return p2_rest<T, N, B, NS * R, TH, false>(out, in, tw);
+    }
   }
 }
 
@@ -1362,20 +1392,34 @@ __device__ __forceinline__ void p2_load_block(const T* __restrict__ src, cplx<T>
   }
 }
 
-// Threads of a power-of-two row CTA: one first-stage butterfly of one sequence each.
-template <int LOGN, int B>
+// One transform buffer, stages in place, for FP32 CTAs of N B / 8 = 1024 first-stage
+// butterflies (2048-point rows with four class pairs, 4096-point rows with two): they take 512
+// threads and half the shared memory, so that two CTAs share an SM and one CTA's loads overlap
+// the other's transform. Other shapes ping-pong between two buffers.
+template <typename T, int LOGN, int B>
+__host__ __device__ constexpr bool p2_onebuf() {
+  return sizeof(T) == 4 && (1 << LOGN) / 8 * B == 1024;
+}
+inline bool p2_onebuf_rt(size_t tsize, int N, int B) { return tsize == 4 && N / 8 * B == 1024; }
+
+// Threads of a power-of-two row CTA: one first-stage butterfly of one sequence each (at most
+// 1024; 512 with one buffer).
+template <typename T, int LOGN, int B>
 __host__ __device__ constexpr int p2_threads() {
-  return ((1 << LOGN) / 8 * B) > 1024 ? 1024 : ((1 << LOGN) / 8 * B);
+  return p2_onebuf<T, LOGN, B>() ? 512
+                                 : (((1 << LOGN) / 8 * B) > 1024 ? 1024 : ((1 << LOGN) / 8 * B));
 }
 
 template <typename T, int LOGN, int B>
-__global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const RowArgs<T> a) {
+__global__ void __launch_bounds__(p2_threads<T, LOGN, B>(), p2_onebuf<T, LOGN, B>() ? 2 : 0)
+    k_row_forward_p2(const RowArgs<T> a) {
   using C = cplx<T>;
   constexpr int N = 1 << LOGN;
   constexpr int NB = N / 8;
+  constexpr bool ONE = p2_onebuf<T, LOGN, B>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  C* Y = X + padded_elems<T>((size_t)N * B);
+  C* Y = ONE ? X : X + padded_elems<T>((size_t)N * B);
   const int y = blockIdx.y;
   const int q0 = blockIdx.x * B;
   const int c0 = 2 * q0;
@@ -1445,7 +1489,7 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const 
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8, p2_threads<LOGN, B>()>(Y, X, tw);
+  const C* R = p2_rest<T, N, B, 8, p2_threads<T, LOGN, B>(), ONE>(Y, X, tw);
   pdl_trigger();
   // unpack the two real spectra of each pair (as k_row_forward)
   for (int i = threadIdx.x; i < (N / 2 + 1) * B; i += blockDim.x) {
@@ -1461,14 +1505,16 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_forward_p2(const 
 }
 
 template <typename T, int LOGN, int B>
-__global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_inverse_p2(const RowArgs<T> a) {
+__global__ void __launch_bounds__(p2_threads<T, LOGN, B>(), p2_onebuf<T, LOGN, B>() ? 2 : 0)
+    k_row_inverse_p2(const RowArgs<T> a) {
   using C = cplx<T>;
   constexpr int N = 1 << LOGN;
   constexpr int NB = N / 8;
   constexpr int WH = N / 2 + 1;
+  constexpr bool ONE = p2_onebuf<T, LOGN, B>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* X = reinterpret_cast<C*>(smem_raw);
-  C* Y = X + padded_elems<T>((size_t)N * B);
+  C* Y = ONE ? X : X + padded_elems<T>((size_t)N * B);
   const int y = blockIdx.y;
   const int q0 = blockIdx.x * B;
   const C* tw = a.pl.tw;
@@ -1492,7 +1538,7 @@ __global__ void __launch_bounds__(p2_threads<LOGN, B>()) k_row_inverse_p2(const 
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8, p2_threads<LOGN, B>()>(Y, X, tw);
+  const C* R = p2_rest<T, N, B, 8, p2_threads<T, LOGN, B>(), ONE>(Y, X, tw);
   pdl_trigger();
   const T inv = T(1) / T(N);
   constexpr int VE = 16 / sizeof(T);
@@ -1537,7 +1583,7 @@ inline bool p2_ok(int N, int blue, int QB, int K) {
 }
 template <typename T>
 inline size_t p2_smem_bytes(int N, int QB) {
-  return sizeof(cplx<T>) * 2 * padded_elems<T>((size_t)N * QB);
+  return sizeof(cplx<T>) * (p2_onebuf_rt(sizeof(T), N, QB) ? 1 : 2) * padded_elems<T>((size_t)N * QB);
 }
 
 // ---------------------------------------------------------------- host-side launch helpers
@@ -1803,11 +1849,11 @@ cudaError_t launch_row_p2_inst(bool forward, const RowArgs<T>& a, dim3 grid, siz
   if (forward) {
     if ((e = grant_smem(k_row_forward_p2<T, LOGN, B>, smem, RowP2Grant<T, LOGN, B>::f)) != cudaSuccess)
       return e;
-    return launch_pdl(k_row_forward_p2<T, LOGN, B>, grid, dim3(p2_threads<LOGN, B>()), smem, st, a);
+    return launch_pdl(k_row_forward_p2<T, LOGN, B>, grid, dim3(p2_threads<T, LOGN, B>()), smem, st, a);
   }
   if ((e = grant_smem(k_row_inverse_p2<T, LOGN, B>, smem, RowP2Grant<T, LOGN, B>::i)) != cudaSuccess)
     return e;
-  return launch_pdl(k_row_inverse_p2<T, LOGN, B>, grid, dim3(p2_threads<LOGN, B>()), smem, st, a);
+  return launch_pdl(k_row_inverse_p2<T, LOGN, B>, grid, dim3(p2_threads<T, LOGN, B>()), smem, st, a);
 }
 
 template <typename T, int LOGN>

@@ -32,8 +32,10 @@ def _pair(B, H, W, K, M, prec, row_pairs=0, lam=1.5):
     (37, 512, 16, 1, "fp32", 1),    # one pair per CTA: 8-byte loads and stores
     (29, 1024, 16, 1, "fp32", 2),   # radix 8, 8, 8, 2
     (45, 2048, 16, 1, "fp32", 2),   # radix 8, 8, 8, 4 (the 2048 x 2048 workload's rows)
-    (21, 2048, 8, 2, "fp32", 4),    # four pairs per CTA, 5x5 patch
+    (21, 2048, 8, 2, "fp32", 4),    # four pairs per CTA, 5x5 patch: one buffer, stages in place
+    (27, 2048, 16, 1, "fp32", 4),   # the 2048 x 2048 workload's row CTAs (one buffer)
     (19, 4096, 4, 1, "fp32", 1),    # 4096-point rows
+    (13, 4096, 4, 1, "fp32", 2),    # 4096-point rows, two pairs: one buffer, stages in place
     (23, 512, 8, 1, "fp64", 2),     # FP64: 16-byte pairs
     (17, 1024, 4, 0, "fp64", 1),
 ])
