@@ -316,8 +316,10 @@ int segsalsa_str_traffic_model(const segsalsa_str_t* h, double* sweep_bytes,
  *                 current unit is transformed; 3 = power-of-two rows (W = 256 ... 4096, no
  *                 Bluestein, K a multiple of 2 row_pairs): compile-time transform plan with
  *                 the first stage computed straight from the loaded row (rows that do not
- *                 qualify run form 1); 0 = the library's choice (3 where it applies, else 1).
- *                 All forms give the same results. */
+ *                 qualify run form 1; in FP32, CTAs of 1024 first-stage butterflies take
+ *                 512 threads and transform in place in one buffer, two CTAs per SM);
+ *                 0 = the library's choice (3 for rows of 2048 and more where it applies,
+ *                 else 1). All forms give the same results. */
 typedef struct {
   int32_t tile_rows;
   int32_t row_pairs;
