@@ -1272,15 +1272,12 @@ __device__ __forceinline__ void p2_load(const cplx<T>* __restrict__ Xin, int it,
   }
 }
 template <typename T, int N, int B, int R, int NS>
-__device__ __forceinline__ void p2_butterfly(cplx<T>* __restrict__ Xout, int it, cplx<T> (&v)[R],
-                                             const cplx<T>* __restrict__ tw) {
+__device__ __forceinline__ void p2_twdft(int it, cplx<T> (&v)[R], const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int NB = N / R;
   constexpr int STRIDE = NB / NS;
-  constexpr int PP = 1 << PadShift<T>::v;
-  const int t = it / B, b = it - t * B;
-  const int g = t / NS;
-  const int j = t - g * NS;
+  const int t = it / B;
+  const int j = t - (t / NS) * NS;
   if constexpr (NS > 1) {
     const C w1 = tw[j * STRIDE];
     v[1] = cmul(v[1], w1);
@@ -1301,6 +1298,16 @@ __device__ __forceinline__ void p2_butterfly(cplx<T>* __restrict__ Xout, int it,
     }
   }
   Dft<R, C>::run(v);
+}
+template <typename T, int N, int B, int R, int NS>
+__device__ __forceinline__ void p2_butterfly(cplx<T>* __restrict__ Xout, int it, cplx<T> (&v)[R],
+                                             const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int PP = 1 << PadShift<T>::v;
+  p2_twdft<T, N, B, R, NS>(it, v, tw);
+  const int t = it / B, b = it - t * B;
+  const int g = t / NS;
+  const int j = t - g * NS;
   const int base = (g * NS * R + j) * B + b;
   if constexpr ((NS * B) % PP == 0) {
     constexpr int SO = NS * B + NS * B / PP;
@@ -1338,22 +1345,109 @@ __device__ __forceinline__ void p2_stage(const cplx<T>* Xin, cplx<T>* Xout, cons
   }
 }
 
+// Radix of the plan's stage with Ns = NS (radix 8 while it fits, then one radix-4 or radix-2
+// stage), and of its last stage.
+template <int N, int NS>
+__host__ __device__ constexpr int p2_radix() {
+  return (N / NS >= 8) ? 8 : (N / NS == 4 ? 4 : 2);
+}
+template <int N, int NS = 8>
+__host__ __device__ constexpr int p2_last_radix() {
+  if constexpr (NS * p2_radix<N, NS>() == N) return p2_radix<N, NS>();
+  else return p2_last_radix<N, NS * p2_radix<N, NS>()>();
+}
+
 // The stages after the first (Ns = NS onwards), ping-ponging between two buffers, or in place
-// in one (ONE); returns the result buffer.
-template <typename T, int N, int B, int NS, int TH, bool ONE>
+// in one (ONE); returns the result buffer. LAST: the last stage is left to the caller, and the
+// buffer holding its input is returned.
+template <typename T, int N, int B, int NS, int TH, bool ONE, bool LAST>
 __device__ __forceinline__ cplx<T>* p2_rest(cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
-  if constexpr (NS == N) {
+  constexpr int R = p2_radix<N, NS>();
+  if constexpr (NS == N || (LAST && NS * R == N)) {
     return in;
   } else {
-    constexpr int R = (N / NS >= 8) ? 8 : (N / NS == 4 ? 4 : 2);
     if constexpr (ONE) {
       p2_stage<T, N, B, R, NS, TH, true>(in, in, tw);
       __syncthreads();
-      return p2_rest<T, N, B, NS * R, TH, true>(in, in, tw);
+      return p2_rest<T, N, B, NS * R, TH, true, LAST>(in, in, tw);
     } else {
       p2_stage<T, N, B, R, NS, TH, false>(in, out, tw);
       __syncthreads();
-      return p2_rest<T, N, B, NS * R, TH, false>(out, in, tw);
+      return p2_rest<T, N, B, NS * R, TH, false, LAST>(out, in, tw);
+    }
+  }
+}
+
+// Forward last stage (radix R, Ns = N / R) fused with the unpack of the two real spectra of each
+// pair: output r of butterfly j is bin k = j + r N/R, and its mirror N - k is output R - 1 - r of
+// butterfly N/R - j (for j = 0, output (R - r) mod R of butterfly 0). The thread that transforms
+// butterfly j also transforms N/R - j (butterflies 0 and N/(2R), their own mirrors, go
+// together), so the unpack reads its two values from registers instead of the buffer. Needs
+// two or more butterflies a thread (N/R B >= 2 TH).
+template <typename T>
+__device__ __forceinline__ void p2_emit_pair(cplx<T>* dst, cplx<T> u, cplx<T> w) {
+  cplx<T> oa, ob;
+  oa.x = T(0.5) * (u.x + w.x); oa.y = T(0.5) * (u.y - w.y);
+  ob.x = T(0.5) * (u.y + w.y); ob.y = T(0.5) * (w.x - u.x);
+  store_pair(dst, oa, ob);
+}
+template <typename T, int N, int B, int TH>
+__device__ __forceinline__ void p2_last_unpack(const cplx<T>* __restrict__ X,
+                                               const cplx<T>* __restrict__ tw,
+                                               cplx<T>* __restrict__ dst, int K) {
+  using C = cplx<T>;
+  constexpr int R = p2_last_radix<N>();
+  constexpr int NS = N / R;
+  constexpr int UPT = NS * B / (2 * TH);
+  static_assert(UPT >= 1 && NS * B % (2 * TH) == 0, "two or more butterflies a thread");
+  const int b = threadIdx.x % B, p = threadIdx.x / B;
+  dst += 2 * b;
+#pragma unroll
+  for (int u = 0; u < UPT; ++u) {
+    const int q = p + u * (TH / B);
+    const int j1 = q, j2 = q == 0 ? NS / 2 : NS - q;
+    C v1[R], v2[R];
+    p2_load<T, N, B, R>(X, j1 * B + b, v1);
+    p2_load<T, N, B, R>(X, j2 * B + b, v2);
+    p2_twdft<T, N, B, R, NS>(j1 * B + b, v1, tw);
+    p2_twdft<T, N, B, R, NS>(j2 * B + b, v2, tw);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k1 = j1 + r * NS, k2 = j2 + r * NS;
+      if (k1 <= N / 2)
+        p2_emit_pair<T>(dst + (size_t)k1 * K, v1[r], q == 0 ? v1[(R - r) % R] : v2[R - 1 - r]);
+      if (k2 <= N / 2)
+        p2_emit_pair<T>(dst + (size_t)k2 * K, v2[r], q == 0 ? v2[R - 1 - r] : v1[R - 1 - r]);
+    }
+  }
+}
+
+// Inverse last stage fused with the output: output r of butterfly (t, b) is pixel t + r N/R of
+// pair b, written as conj(v) / N straight from registers.
+template <typename T, int N, int B, int TH>
+__device__ __forceinline__ void p2_last_store(const cplx<T>* __restrict__ X,
+                                              const cplx<T>* __restrict__ tw,
+                                              T* __restrict__ zrow, int K) {
+  using C = cplx<T>;
+  constexpr int R = p2_last_radix<N>();
+  constexpr int NS = N / R;
+  constexpr int IPT = NS * B / TH;
+  static_assert(IPT >= 1 && NS * B % TH == 0, "whole butterflies per thread");
+  const T inv = T(1) / T(N);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const int it = threadIdx.x + u * TH;
+    const int t = it / B, b = it - t * B;
+    C v[R];
+    p2_load<T, N, B, R>(X, it, v);
+    p2_twdft<T, N, B, R, NS>(it, v, tw);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T* d = zrow + (size_t)(t + r * NS) * K + 2 * b;
+      if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float2*>(d) = make_float2(v[r].x * inv, -v[r].y * inv);
+      else
+        *reinterpret_cast<double2*>(d) = make_double2(v[r].x * inv, -v[r].y * inv);
     }
   }
 }
@@ -1489,18 +1583,21 @@ __global__ void __launch_bounds__(p2_threads<T, LOGN, B>(), p2_onebuf<T, LOGN, B
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8, p2_threads<T, LOGN, B>(), ONE>(Y, X, tw);
+  constexpr int TH = p2_threads<T, LOGN, B>();
+  constexpr bool FUSE = N / p2_last_radix<N>() * B >= 2 * TH;
+  const C* R = p2_rest<T, N, B, 8, TH, ONE, FUSE>(Y, X, tw);
   pdl_trigger();
-  // unpack the two real spectra of each pair (as k_row_forward)
-  for (int i = threadIdx.x; i < (N / 2 + 1) * B; i += blockDim.x) {
-    const int qq = i % B;
-    const int kx = i / B;
-    const C u = R[px<T>(kx * B + qq)];
-    const C w = R[px<T>(((kx == 0) ? 0 : N - kx) * B + qq)];
-    C oa, ob;
-    oa.x = T(0.5) * (u.x + w.x); oa.y = T(0.5) * (u.y - w.y);
-    ob.x = T(0.5) * (u.y + w.y); ob.y = T(0.5) * (w.x - u.x);
-    store_pair(a.S + ((size_t)y * a.Wh + kx) * a.K + 2 * (q0 + qq), oa, ob);
+  if constexpr (FUSE) {
+    p2_last_unpack<T, N, B, TH>(R, tw, a.S + (size_t)y * a.Wh * a.K + 2 * q0, a.K);
+  } else {
+    // unpack the two real spectra of each pair (as k_row_forward)
+    for (int i = threadIdx.x; i < (N / 2 + 1) * B; i += blockDim.x) {
+      const int qq = i % B;
+      const int kx = i / B;
+      const C u = R[px<T>(kx * B + qq)];
+      const C w = R[px<T>(((kx == 0) ? 0 : N - kx) * B + qq)];
+      p2_emit_pair<T>(a.S + ((size_t)y * a.Wh + kx) * a.K + 2 * (q0 + qq), u, w);
+    }
   }
 }
 
@@ -1538,34 +1635,10 @@ __global__ void __launch_bounds__(p2_threads<T, LOGN, B>(), p2_onebuf<T, LOGN, B
     p2_first<T, N, B>(v, t, q, Y);
   }
   __syncthreads();
-  const C* R = p2_rest<T, N, B, 8, p2_threads<T, LOGN, B>(), ONE>(Y, X, tw);
+  constexpr int TH = p2_threads<T, LOGN, B>();
+  const C* R = p2_rest<T, N, B, 8, TH, ONE, true>(Y, X, tw);
   pdl_trigger();
-  const T inv = T(1) / T(N);
-  constexpr int VE = 16 / sizeof(T);
-  if constexpr ((2 * B) % VE == 0) {
-    constexpr int NV = 2 * B / VE;
-    for (int i = threadIdx.x; i < N * NV; i += blockDim.x) {
-      const int x = i / NV, j = i - x * NV;
-      T o[VE];
-#pragma unroll
-      for (int e = 0; e < VE / 2; ++e) {
-        const C v = R[px<T>(x * B + j * (VE / 2) + e)];   // conj(v) / N
-        o[2 * e] = v.x * inv;
-        o[2 * e + 1] = -v.y * inv;
-      }
-      T* dst = a.z + ((size_t)y * N + x) * a.K + 2 * q0 + j * VE;
-      if constexpr (sizeof(T) == 4)
-        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-      else
-        *reinterpret_cast<double2*>(dst) = make_double2(o[0], o[1]);
-    }
-  } else {  // FP32, B = 1: 8-byte stores
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-      const C v = R[px<T>(x)];
-      *reinterpret_cast<float2*>(a.z + ((size_t)y * N + x) * a.K + 2 * q0) =
-          make_float2(v.x * inv, -v.y * inv);
-    }
-  }
+  p2_last_store<T, N, B, TH>(R, tw, a.z + (size_t)y * N * a.K + 2 * q0, a.K);
 }
 
 // Whether a row plan can run the power-of-two kernels: N = 2^LOGN with 256 <= N <= 4096, no
