@@ -38,6 +38,7 @@ def _pair(B, H, W, K, M, prec, row_pairs=0, lam=1.5):
     (13, 4096, 4, 1, "fp32", 2),    # 4096-point rows, two pairs: one buffer, stages in place
     (23, 512, 8, 1, "fp64", 2),     # FP64: 16-byte pairs
     (17, 1024, 4, 0, "fp64", 1),
+    (9, 4096, 4, 1, "fp64", 1),     # FP64 4096-point rows (radix-8 last stage)
 ])
 def test_power_of_two_row_passes_match(B, H, W, K, M, prec, rp):
     """Form 3 (compile-time plan, first stage fused into the load) against form 1: the
