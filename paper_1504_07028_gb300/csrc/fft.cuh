@@ -1673,7 +1673,7 @@ struct RowLaunch {
 inline int row_pairs_per_cta(int Mf, int Q, int rows = 1 << 30, int max_elems = 4096) {
   int qb = 1;
   while (qb < Q && 2 * qb * Mf <= max_elems) qb *= 2;
-  while (qb > 1 && (long long)rows * ((Q + qb - 1) / qb) < 152 && Mf * qb / 2 >= 128) qb /= 2;
+  while (qb > 1 && (long long)rows * ((Q + qb - 1) / qb) < 2 * 152 && Mf * qb / 2 >= 128) qb /= 2;
   return qb;
 }
 

@@ -268,9 +268,11 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   }
   if (pl.Mf > 8192) { msg = "row length too large for the shared-memory FFT"; return SEGSALSA_ERR_ARG; }
   const int Q = (K + 1) / 2;
-  // small images (latency bound): fewer class pairs per CTA until the grid has one CTA per SM
-  // (a target of eight per SM, i.e. one pair per CTA, measured 12 % slower at 145 x 145, K = 16);
-  // larger ones: as many as fit (contiguous 64-byte pixel reads, fewer CTAs)
+  // small images (latency bound): fewer class pairs per CTA until the grid has two CTAs per SM
+  // (145 x 145, K = 16: two pairs per CTA, 33.4 us per iteration of one solve against 35.0 us
+  // with four pairs, one CTA per SM; a target of eight per SM, one pair per CTA, measured 12 %
+  // slower with earlier kernels); larger ones: as many as fit (contiguous 64-byte pixel reads,
+  // fewer CTAs)
   const bool small_image = (long long)H * W < 65536;
   pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
   if (tl && tl->row_pairs) {
