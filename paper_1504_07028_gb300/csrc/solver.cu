@@ -276,7 +276,7 @@ static int make_plan(const segsalsa_str_params* pr, Plan& pl, std::string& msg,
   const bool small_image = (long long)H * W < 65536;
   pl.QB = row_pairs_per_cta(pl.Mf, Q, small_image ? H : (1 << 30));
   if (tl && tl->row_pairs) {
-    const int qmax = row_pairs_per_cta(pl.Mf, Q, 1 << 30, 8192 * 4 / (int)sizeof(T));  // the most a CTA takes
+    const int qmax = row_pairs_per_cta(pl.Mf, Q, 1 << 30, 8192 * 4 / (int)sizeof(T), false);  // the most a CTA takes
     pl.QB = std::min(floor_pow2(tl->row_pairs), qmax);
   }
   pl.nqblk = (Q + pl.QB - 1) / pl.QB;
