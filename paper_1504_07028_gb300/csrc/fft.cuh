@@ -1553,7 +1553,7 @@ __global__ void __launch_bounds__(p2_threads<T, LOGN, B>(), p2_onebuf<T, LOGN, B
       // p00 (+ p01) (+ p10) (+ p11), the order of gather_row16. All loads of the butterfly
       // are issued before any sum (an absent cover aliases the first, its value is dropped),
       // so that they are in flight together.
-      // (in two batches of four pixels, within the register budget of a 1024-thread CTA)
+      // (in two batches of four pixels, within 64 registers a thread)
       const int rb1a = rb1;
 #pragma unroll
       for (int h = 0; h < 8; h += 4) {
