@@ -275,9 +275,17 @@ __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* ome
                                                       int K, int sp, double* part) {
   constexpr int P = 2 * M + 1;
   constexpr int RH = PRIOR_TH + 2 * M, RW = PRIOR_TW + 2 * M;
+  // Where it fits, the tile's projected z (the tile, its halo and one more row and column for
+  // the forward differences) is first copied into shared memory, each pixel read once from
+  // global memory instead of three times; pixels padded by one 16-byte chunk so that
+  // consecutive pixels' chunks fall on different banks. Same differences, same sums.
+  constexpr int VE = 16 / sizeof(T);
+  constexpr int ZH = RH + 1, ZW = RW + 1, PS = G + VE;
+  constexpr bool ZTILE = (size_t)ZH * ZW * PS * sizeof(T) <= 32 * 1024;
   __shared__ double red32[32];
   __shared__ T sA[RH * RW], sB[RH * RW], sC[RH * RW];
   __shared__ T w2[P * P];
+  __shared__ __align__(16) T sZ[ZTILE ? ZH * ZW * PS : VE];
   for (int j = threadIdx.x; j < P * P; j += blockDim.x) w2[j] = omega[j] * omega[j];
   const int ntx = (W + PRIOR_TW - 1) / PRIOR_TW;
   const int ntiles = ((H + PRIOR_TH - 1) / PRIOR_TH) * ntx;
@@ -285,34 +293,75 @@ __global__ void __launch_bounds__(AUX_THREADS) k_prior(const T* zp, const T* ome
   pdl_wait();
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int y0 = (tile / ntx) * PRIOR_TH, x0 = (tile % ntx) * PRIOR_TW;
-    __syncthreads();  // the previous tile's reads of sA/sB/sC are done (and w2 is written)
-    for (int r = threadIdx.x; r < RH * RW; r += blockDim.x) {
-      const int ry = r / RW, rx = r - ry * RW;
-      const int y = wrap_near(y0 - M + ry, H), x = wrap_near(x0 - M + rx, W);  // M < H, W
-      const int xh = x + 1 == W ? 0 : x + 1, yv = y + 1 == H ? 0 : y + 1;
-      constexpr int VE = 16 / sizeof(T);
-      const T* rc = zp + ((size_t)y * W + x) * K;
-      const T* rh = zp + ((size_t)y * W + xh) * K;
-      const T* rv = zp + ((size_t)yv * W + x) * K;
-      T a = T(0), b = T(0), c = T(0);
+    __syncthreads();  // the previous tile's reads of sA/sB/sC (and sZ) are done, w2 written
+    if constexpr (ZTILE) {
+      constexpr int NCH = G / VE;
+      for (int i = threadIdx.x; i < ZH * ZW * NCH; i += blockDim.x) {
+        const int pix = i / NCH, ch = i - pix * NCH;
+        const int ry = pix / ZW, rx = pix - ry * ZW;
+        const int y = wrap_near(y0 - M + ry, H), x = wrap_near(x0 - M + rx, W);
+        T cz[VE];
+        if (ch * VE < K) {
+          load_chunk<T>(zp + ((size_t)y * W + x) * K, ch * VE, K, cz);
+        } else {
 #pragma unroll
-      for (int k0 = 0; k0 < G; k0 += VE) {
-        if (k0 >= K) break;
-        T zc[VE], zh[VE], zv[VE];
-        load_chunk<T>(rc, k0, K, zc);
-        load_chunk<T>(rh, k0, K, zh);
-        load_chunk<T>(rv, k0, K, zv);
-#pragma unroll
-        for (int e = 0; e < VE; ++e) {
-          const T h = zh[e] - zc[e], v = zv[e] - zc[e];
-          a += h * h;
-          b += h * v;
-          c += v * v;
+          for (int e = 0; e < VE; ++e) cz[e] = T(0);
         }
+        T* dz = sZ + pix * PS + ch * VE;
+        if constexpr (sizeof(T) == 4)
+          *reinterpret_cast<float4*>(dz) = make_float4(cz[0], cz[1], cz[2], cz[3]);
+        else
+          *reinterpret_cast<double2*>(dz) = make_double2(cz[0], cz[1]);
       }
-      sA[r] = a;
-      sB[r] = b;
-      sC[r] = c;
+      __syncthreads();
+      for (int r = threadIdx.x; r < RH * RW; r += blockDim.x) {
+        const int ry = r / RW, rx = r - ry * RW;
+        const T* zc = sZ + (ry * ZW + rx) * PS;   // pixel (ry, rx); + PS: (ry, rx + 1)
+        const T* zv = zc + ZW * PS;               // (ry + 1, rx)
+        T a = T(0), b = T(0), c = T(0);
+#pragma unroll
+        for (int k0 = 0; k0 < G; k0 += VE) {
+          if (k0 >= K) break;
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            const T h = zc[PS + k0 + e] - zc[k0 + e], v = zv[k0 + e] - zc[k0 + e];
+            a += h * h;
+            b += h * v;
+            c += v * v;
+          }
+        }
+        sA[r] = a;
+        sB[r] = b;
+        sC[r] = c;
+      }
+    } else {
+      for (int r = threadIdx.x; r < RH * RW; r += blockDim.x) {
+        const int ry = r / RW, rx = r - ry * RW;
+        const int y = wrap_near(y0 - M + ry, H), x = wrap_near(x0 - M + rx, W);  // M < H, W
+        const int xh = x + 1 == W ? 0 : x + 1, yv = y + 1 == H ? 0 : y + 1;
+        const T* rc = zp + ((size_t)y * W + x) * K;
+        const T* rh = zp + ((size_t)y * W + xh) * K;
+        const T* rv = zp + ((size_t)yv * W + x) * K;
+        T a = T(0), b = T(0), c = T(0);
+#pragma unroll
+        for (int k0 = 0; k0 < G; k0 += VE) {
+          if (k0 >= K) break;
+          T zc[VE], zh[VE], zv[VE];
+          load_chunk<T>(rc, k0, K, zc);
+          load_chunk<T>(rh, k0, K, zh);
+          load_chunk<T>(rv, k0, K, zv);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) {
+            const T h = zh[e] - zc[e], v = zv[e] - zc[e];
+            a += h * h;
+            b += h * v;
+            c += v * v;
+          }
+        }
+        sA[r] = a;
+        sB[r] = b;
+        sC[r] = c;
+      }
     }
     __syncthreads();
     const int ty = threadIdx.x / PRIOR_TW, tx = threadIdx.x - ty * PRIOR_TW;
@@ -367,6 +416,27 @@ inline void launch_prior_m(int G, int blocks, cudaStream_t st, const T* zp, cons
     case 8: launch_pdl(k_prior<T, M, 8>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
     case 16: launch_pdl(k_prior<T, M, 16>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
     default: launch_pdl(k_prior<T, M, 32>, dim3(blocks), dim3(AUX_THREADS), 0, st, zp, om, H, W, K, sp, part); break;
+  }
+}
+template <typename T, int M>
+inline cudaError_t prior_blocks_per_sm_m(int G, int* nb) {
+  switch (G) {
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_prior<T, M, 4>, AUX_THREADS, 0);
+    case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_prior<T, M, 8>, AUX_THREADS, 0);
+    case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_prior<T, M, 16>, AUX_THREADS, 0);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_prior<T, M, 32>, AUX_THREADS, 0);
+  }
+}
+// Resident blocks per SM of the prior kernel (its tile loop is sized to one wave of them).
+template <typename T>
+inline cudaError_t prior_blocks_per_sm(int M, int G, int* nb) {
+  switch (M) {
+    case 0: return prior_blocks_per_sm_m<T, 0>(G, nb);
+    case 1: return prior_blocks_per_sm_m<T, 1>(G, nb);
+    case 2: return prior_blocks_per_sm_m<T, 2>(G, nb);
+    case 3: return prior_blocks_per_sm_m<T, 3>(G, nb);
+    case 4: return prior_blocks_per_sm_m<T, 4>(G, nb);
+    default: return prior_blocks_per_sm_m<T, 5>(G, nb);
   }
 }
 template <typename T>

@@ -582,6 +582,15 @@ class Solver : public SolverBase {
       pl.zs_grid = (int)std::min<long long>(most, (long long)nb * nsm);
       if (nb < 1) pl.zs = 0;
     }
+    {
+      // the prior's blocks walk the tiles: one wave of them, so that no SM runs a second
+      // round of blocks after the others are done (never more than the planned partials)
+      int dev = 0, nsm = 0, nb = 0;
+      SGS_CUDA(cudaGetDevice(&dev));
+      SGS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      SGS_CUDA(prior_blocks_per_sm<T>(pl.M, pl.G, &nb));
+      if (nb >= 1) pl.nprior_blk = std::max(1, std::min(pl.nprior_blk, nb * nsm));
+    }
     if (pl.rp) {
       // one wave of persistent CTAs; three launches of the one-unit kernels if none fits
       int dev = 0, nsm = 0, nbf = 0, nbi = 0;
